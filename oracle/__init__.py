@@ -1,0 +1,265 @@
+"""FP64 CPU oracle for the logistic-GLM log-posterior and gradient.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / ``--impl reference`` legs may import this
+package; the library under ``paper_1310_1537_gb300`` never does. The oracle
+shares no code with the CUDA path. The arithmetic lives in ``glm_oracle.c``
+(plain single-threaded C, FP64); this module only compiles it with gcc and
+marshals numpy arrays through ctypes.
+
+Functions and the passages they follow:
+
+* ``logpost_grad``         — §3.1.1 log-likelihood (eq-loglike-binlogit),
+  §4.2 gradient (eq-grad-expanded / eq-grad-compact), Gaussian prior N(0, s^2 I).
+* ``loglik_partial``       — the same likelihood sums over a row range (the
+  per-worker partials that the §4.2.2 reduction combines).
+* ``logpost_grad_grouped`` — §4.1 hierarchical GLM, per-group L_m with prior
+  N(mu, tau^2 I).
+* ``rwm``                  — random-walk Metropolis consumer of the
+  log-posterior (§2.2, §3.4.4); FP32 state, FP64 acceptance.
+* ``bf16_from_f32``, ``quantize_e4m3``, ``e4m3_value`` — reduced-precision
+  storage of X (bfloat16 RNE; OCP E4M3 with power-of-two column scales).
+
+Every function is pinned by ``tests/test_oracle_pins.py`` against closed
+forms, extended-precision brute force, finite differences, symmetries,
+library routines and quadrature.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "glm_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile glm_oracle.c into liboracle.so with gcc (-O2, no fast-math)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        dp = C.POINTER(C.c_double)
+        fp = C.POINTER(C.c_float)
+        u8 = C.POINTER(C.c_uint8)
+        u16 = C.POINTER(C.c_uint16)
+        i64p = C.POINTER(C.c_int64)
+        lib.oracle_logpost_grad.argtypes = [dp, C.c_int64, C.c_int32, C.c_int64, u8, dp,
+                                            C.c_int32, C.c_double, dp, dp]
+        lib.oracle_loglik_partial.argtypes = [dp, C.c_int64, C.c_int64, C.c_int32, C.c_int64,
+                                              u8, dp, C.c_int32, dp, dp]
+        lib.oracle_logpost_grad_grouped.argtypes = [dp, C.c_int32, C.c_int64, u8, i64p,
+                                                    C.c_int32, dp, dp, C.c_double, dp, dp]
+        lib.oracle_rwm.argtypes = [dp, C.c_int64, C.c_int32, C.c_int64, u8, C.c_double,
+                                   C.c_int32, C.c_int32, C.c_float, fp, dp, fp, dp,
+                                   C.c_int32, fp, u8, dp, dp]
+        lib.oracle_bf16_from_f32.argtypes = [fp, C.c_int64, u16]
+        lib.oracle_bf16_from_f32.restype = None
+        lib.oracle_bf16_to_f64.argtypes = [u16, C.c_int64, dp]
+        lib.oracle_bf16_to_f64.restype = None
+        lib.oracle_e4m3_value.argtypes = [C.c_uint8]
+        lib.oracle_e4m3_value.restype = C.c_double
+        lib.oracle_e4m3_from_f64.argtypes = [C.c_double]
+        lib.oracle_e4m3_from_f64.restype = C.c_uint8
+        lib.oracle_e4m3_column_scale.argtypes = [C.c_double]
+        lib.oracle_e4m3_column_scale.restype = C.c_double
+        lib.oracle_quantize_e4m3.argtypes = [fp, C.c_int64, C.c_int32, C.c_int64, u8,
+                                             C.c_int64, fp]
+        for name in ("oracle_logpost_grad", "oracle_loglik_partial",
+                     "oracle_logpost_grad_grouped", "oracle_rwm", "oracle_quantize_e4m3"):
+            getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _p(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _f64_matrix(X):
+    X = np.asarray(X)
+    if X.ndim != 2:
+        raise ValueError("X must be 2-D (N x ld)")
+    return np.ascontiguousarray(X, dtype=np.float64)
+
+
+def logpost_grad(X, y, beta, prior_sigma=10.0, p=None):
+    """f (K,) and g (K, P) of the Bayesian logistic log-posterior, FP64.
+
+    X: N x ld (first ``p`` columns used, default all); y: N uint8 in {0,1};
+    beta: (P,) or (K, P).
+    """
+    Xd = _f64_matrix(X)
+    n, ld = Xd.shape
+    b = np.ascontiguousarray(np.atleast_2d(beta), dtype=np.float64)
+    k, pp = b.shape
+    P = pp if p is None else int(p)
+    if P != pp or P > ld:
+        raise ValueError("beta width must equal P <= ld")
+    yy = np.ascontiguousarray(y, dtype=np.uint8)
+    if yy.shape[0] != n:
+        raise ValueError("y length must equal N")
+    f = np.empty(k, dtype=np.float64)
+    g = np.empty((k, P), dtype=np.float64)
+    rc = _load().oracle_logpost_grad(_p(Xd, C.c_double), n, P, ld, _p(yy, C.c_uint8),
+                                     _p(b, C.c_double), k, float(prior_sigma),
+                                     _p(f, C.c_double), _p(g, C.c_double))
+    if rc != 0:
+        raise ValueError("oracle_logpost_grad rejected its arguments")
+    return f, g
+
+
+def loglik_partial(X, y, beta, r0, r1, p=None):
+    """Likelihood-only sums (no prior) over rows [r0, r1)."""
+    Xd = _f64_matrix(X)
+    n, ld = Xd.shape
+    b = np.ascontiguousarray(np.atleast_2d(beta), dtype=np.float64)
+    k, P = b.shape
+    yy = np.ascontiguousarray(y, dtype=np.uint8)
+    if not (0 <= r0 <= r1 <= n):
+        raise ValueError("bad row range")
+    f = np.empty(k, dtype=np.float64)
+    g = np.empty((k, P), dtype=np.float64)
+    rc = _load().oracle_loglik_partial(_p(Xd, C.c_double), int(r0), int(r1), P, ld,
+                                       _p(yy, C.c_uint8), _p(b, C.c_double), k,
+                                       _p(f, C.c_double), _p(g, C.c_double))
+    if rc != 0:
+        raise ValueError("oracle_loglik_partial rejected its arguments")
+    return f, g
+
+
+def logpost_grad_grouped(X, y, offsets, beta, mu, tau):
+    """Per-group f (G,) and g (G, P) of the hierarchical logistic GLM."""
+    Xd = _f64_matrix(X)
+    n, ld = Xd.shape
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    G, P = b.shape
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    if off.shape[0] != G + 1 or off[0] < 0 or off[-1] > n:
+        raise ValueError("offsets must have G+1 entries within [0, N]")
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.uint8)
+    f = np.empty(G, dtype=np.float64)
+    g = np.empty((G, P), dtype=np.float64)
+    rc = _load().oracle_logpost_grad_grouped(_p(Xd, C.c_double), P, ld, _p(yy, C.c_uint8),
+                                             _p(off, C.c_int64), G, _p(b, C.c_double),
+                                             _p(m, C.c_double), float(tau),
+                                             _p(f, C.c_double), _p(g, C.c_double))
+    if rc != 0:
+        raise ValueError("oracle_logpost_grad_grouped rejected its arguments")
+    return f, g
+
+
+def rwm(X, y, beta0, z, log_u, step, prior_sigma=10.0, p=None):
+    """Run K random-walk Metropolis chains for z.shape[0] steps.
+
+    beta0: (K, P) float32 start; z: (T, K, P) float32; log_u: (T, K) float64.
+    Returns dict(samples (T,K,P) f32, accept (T,K) u8, logpost (T,K),
+    log_alpha (T,K), beta (K,P) final, f (K,) final, f0 (K,) initial).
+    """
+    Xd = _f64_matrix(X)
+    n, ld = Xd.shape
+    state = np.array(np.atleast_2d(beta0), dtype=np.float32, order="C")
+    k, P = state.shape
+    zz = np.ascontiguousarray(z, dtype=np.float32)
+    lu = np.ascontiguousarray(log_u, dtype=np.float64)
+    T = zz.shape[0]
+    if zz.shape != (T, k, P) or lu.shape != (T, k):
+        raise ValueError("z must be (T,K,P) and log_u (T,K)")
+    yy = np.ascontiguousarray(y, dtype=np.uint8)
+    fs = np.zeros(k, dtype=np.float64)
+    samples = np.empty((T, k, P), dtype=np.float32)
+    acc = np.empty((T, k), dtype=np.uint8)
+    lp = np.empty((T, k), dtype=np.float64)
+    la = np.empty((T, k), dtype=np.float64)
+    lib = _load()
+    # initial log-posterior
+    rc = lib.oracle_rwm(_p(Xd, C.c_double), n, P, ld, _p(yy, C.c_uint8), float(prior_sigma),
+                        k, 0, C.c_float(step), _p(zz, C.c_float), _p(lu, C.c_double),
+                        _p(state, C.c_float), _p(fs, C.c_double), 1, None, None, None, None)
+    if rc != 0:
+        raise ValueError("oracle_rwm rejected its arguments")
+    f0 = fs.copy()
+    rc = lib.oracle_rwm(_p(Xd, C.c_double), n, P, ld, _p(yy, C.c_uint8), float(prior_sigma),
+                        k, T, C.c_float(step), _p(zz, C.c_float), _p(lu, C.c_double),
+                        _p(state, C.c_float), _p(fs, C.c_double), 0, _p(samples, C.c_float),
+                        _p(acc, C.c_uint8), _p(lp, C.c_double), _p(la, C.c_double))
+    if rc != 0:
+        raise ValueError("oracle_rwm rejected its arguments")
+    return {"samples": samples, "accept": acc, "logpost": lp, "log_alpha": la,
+            "beta": state, "f": fs, "f0": f0}
+
+
+def bf16_from_f32(x):
+    """uint16 bit patterns of the nearest-even bfloat16 values of float32 ``x``."""
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(a.shape, dtype=np.uint16)
+    _load().oracle_bf16_from_f32(_p(a, C.c_float), a.size, _p(out, C.c_uint16))
+    return out
+
+
+def bf16_to_f64(bits):
+    b = np.ascontiguousarray(bits, dtype=np.uint16)
+    out = np.empty(b.shape, dtype=np.float64)
+    _load().oracle_bf16_to_f64(_p(b, C.c_uint16), b.size, _p(out, C.c_double))
+    return out
+
+
+def e4m3_value(code: int) -> float:
+    return _load().oracle_e4m3_value(int(code) & 0xFF)
+
+
+def e4m3_from_f64(v: float) -> int:
+    return int(_load().oracle_e4m3_from_f64(float(v)))
+
+
+def e4m3_column_scale(amax: float) -> float:
+    return _load().oracle_e4m3_column_scale(float(amax))
+
+
+def e4m3_decode(codes):
+    """float64 values of an array of E4M3 codes (by the format definition)."""
+    table = np.array([e4m3_value(c) for c in range(256)], dtype=np.float64)
+    return table[np.asarray(codes, dtype=np.uint8)]
+
+
+def quantize_e4m3(X32, p=None, ld_q=None):
+    """(Q uint8 N x ld_q, scale float32 P) from float32 X (N x ld)."""
+    a = np.ascontiguousarray(X32, dtype=np.float32)
+    n, ld = a.shape
+    P = ld if p is None else int(p)
+    lq = P if ld_q is None else int(ld_q)
+    Q = np.empty((n, lq), dtype=np.uint8)
+    s = np.empty(P, dtype=np.float32)
+    rc = _load().oracle_quantize_e4m3(_p(a, C.c_float), n, P, ld, _p(Q, C.c_uint8), lq,
+                                      _p(s, C.c_float))
+    if rc != 0:
+        raise ValueError("oracle_quantize_e4m3 rejected its arguments")
+    return Q, s
+
+
+def dequantize_e4m3(Q, scale, p=None):
+    """FP64 values q * s_j of an E4M3 matrix (first P columns), exactly."""
+    P = len(scale) if p is None else int(p)
+    v = e4m3_decode(Q[:, :P])
+    return v * np.asarray(scale, dtype=np.float64)[None, :P]
