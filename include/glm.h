@@ -1,0 +1,225 @@
+/*
+ * glm.h — C ABI of the GB300 (sm_103a) library for the data-parallel hot path
+ * of Mahani & Sharabiani, "SIMD Parallel MCMC Sampling with Applications for
+ * Big-Data Bayesian Analytics": the Bayesian logistic-regression log-posterior
+ * and its gradient, evaluated for K coefficient vectors in one pass over X.
+ *
+ * What every evaluation computes (for k = 0..K-1, rows n = 0..N-1):
+ *
+ *   eta_nk = x_n . beta_k                                   (§3.2, the LA map)
+ *   f_k    = sum_n -[(1 - y_n) eta_nk + log(1 + exp(-eta_nk))]
+ *            - |beta_k|^2 / (2 s^2) - (P/2) log(2 pi s^2)   (§3.1.1, eq-loglike-binlogit,
+ *                                                             plus the N(0, s^2 I) prior)
+ *   g_k    = sum_n (y_n - 1/(1 + exp(-eta_nk))) x_n - beta_k / s^2
+ *                                                           (§4.2, eq-grad-expanded/-compact)
+ *
+ * Conventions shared by every entry point below:
+ *
+ * - Layout. X is row-major N x ld (row n starts at element n*ld); only the
+ *   first P columns are used, padding columns must hold finite values
+ *   (zeros recommended). ld * element_size must be a multiple of 16 bytes and
+ *   X must be 16-byte aligned. y is N bytes, each 0 or 1 (other values give
+ *   undefined results). beta is K x P row-major FP32 (beta_k contiguous),
+ *   f_out is K FP64, g_out is K x P row-major FP32.
+ * - Storage types. GLM_X_F32: X is float. GLM_X_BF16: X is bfloat16.
+ *   GLM_X_FP8E4M3: X holds E4M3 codes q and x_scale holds P FP32 column
+ *   scales, the stored value being q * x_scale[j]. x_scale must be NULL for
+ *   the other types.
+ * - Memory. Unless an entry point says "host", every data pointer is device
+ *   memory of the handle's device, owned by the caller; the library never
+ *   frees or retains it past the call. The handle owns only its workspace.
+ * - Streams. glm_stream_t is a cudaStream_t (NULL = legacy default stream).
+ *   Device entry points enqueue work and return without synchronising; they
+ *   allocate nothing. One handle may be used by one stream at a time.
+ * - Errors. Argument errors are detected on the host before anything is
+ *   launched and return GLM_ERR_INVALID_ARG / GLM_ERR_UNSUPPORTED. A launch
+ *   failure returns GLM_ERR_CUDA. Asynchronous device-side conditions (a
+ *   bounded wait that expired) are recorded in the handle's status word and
+ *   returned by glm_sync.
+ */
+#ifndef GLM_H
+#define GLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GLM_API __attribute__((visibility("default")))
+#else
+#define GLM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct glm_ctx *glm_handle_t;
+typedef struct CUstream_st *glm_stream_t;   /* same type as cudaStream_t */
+
+typedef enum {
+    GLM_OK = 0,
+    GLM_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or value      */
+    GLM_ERR_UNSUPPORTED = 2,   /* valid but outside what this build supports */
+    GLM_ERR_OOM = 3,           /* workspace allocation failed                 */
+    GLM_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed        */
+    GLM_ERR_TIMEOUT = 5,       /* a device-side bounded wait expired          */
+    GLM_ERR_NO_DEVICE = 6      /* no usable sm_103 device                     */
+} glm_status_t;
+
+typedef enum {
+    GLM_X_F32 = 0,
+    GLM_X_BF16 = 1,
+    GLM_X_FP8E4M3 = 2
+} glm_xtype_t;
+
+/* Handle descriptor: the shape of the dataset the handle evaluates. */
+typedef struct {
+    int64_t n_rows;       /* N >= 0                                           */
+    int32_t p;            /* P >= 1                                           */
+    int32_t ld;           /* row stride in elements, >= P, 16-byte rows       */
+    int32_t k_max;        /* largest K any call will pass, 1..1024            */
+    int32_t xtype;        /* glm_xtype_t                                      */
+    double prior_sigma;   /* s > 0 of the N(0, s^2 I) prior                   */
+    int32_t device;       /* CUDA device ordinal                              */
+    uint32_t flags;       /* GLM_FLAG_* below                                 */
+} glm_desc_t;
+
+/* Never route K > 1 evaluations to the tensor-core kernel. */
+#define GLM_FLAG_NO_TENSOR_CORES 0x1u
+
+/* Read-only facts about a handle (for reports and tuning). */
+typedef struct {
+    int32_t sm_count;         /* SMs of the device                            */
+    int32_t grid;             /* CTAs of the fused CUDA-core kernel           */
+    int32_t tile_rows;        /* rows per staged tile                         */
+    int32_t stages;           /* tiles in flight per CTA                      */
+    int32_t smem_bytes;       /* dynamic shared memory per CTA                */
+    int32_t tc_enabled;       /* 1 if K >= tc_min_k uses tcgen05 tensor cores */
+    int32_t tc_min_k;
+    int64_t workspace_bytes;  /* device memory owned by the handle            */
+} glm_info_t;
+
+/*
+ * glm_create — validate *desc, select the device, allocate the handle's
+ * workspace (per-CTA partial sums, completion ticket, status word) and choose
+ * the kernel configuration. Returns GLM_OK and *out, or an error and
+ * *out = NULL. Not stream-ordered: call it before any capture.
+ */
+GLM_API glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out);
+
+/* glm_destroy — synchronise the device, free the workspace and the handle.
+ * NULL is accepted and ignored. */
+GLM_API glm_status_t glm_destroy(glm_handle_t h);
+
+/* glm_status_str — static English text of a status code. */
+GLM_API const char *glm_status_str(glm_status_t s);
+
+/* glm_get_info — fill *info for handle h. */
+GLM_API glm_status_t glm_get_info(glm_handle_t h, glm_info_t *info);
+
+/*
+ * glm_logpost_grad — log-posterior f_k and gradient g_k (definitions above;
+ * §3.1.1, §4.2) for K coefficient vectors in one fused pass over X, for the
+ * handle's N rows.
+ *   X       device, N x ld of the handle's xtype, 16-byte aligned
+ *   x_scale device, P FP32 column scales for GLM_X_FP8E4M3, else NULL
+ *   y       device, N bytes in {0, 1}
+ *   beta    device, K x P FP32
+ *   K       1 <= K <= k_max
+ *   f_out   device, K FP64 (8-byte aligned)
+ *   g_out   device, K x P FP32
+ * f is accumulated per row in FP32 and across CTAs in FP64; g is accumulated
+ * in FP32 and combined across CTAs in FP64. Results are deterministic: the
+ * same inputs give bitwise the same outputs, whatever else runs. K >= tc_min_k
+ * with BF16/FP8 storage runs on the tcgen05 tensor cores (see glm_get_info).
+ */
+GLM_API glm_status_t glm_logpost_grad(glm_handle_t h, const void *X, const float *x_scale,
+                              const uint8_t *y, const float *beta, int32_t K,
+                              double *f_out, float *g_out, glm_stream_t stream);
+
+/*
+ * glm_logpost_grad_host — the same evaluation with HOST beta and results
+ * (the offload pattern of §4.5: copy beta in, evaluate, copy f and g out).
+ * X, x_scale and y stay device-resident. beta_host (K x P FP32), f_host (K)
+ * and g_host (K x P) are host memory; pinned memory gives the fastest copies.
+ * Synchronises `stream` before returning.
+ */
+GLM_API glm_status_t glm_logpost_grad_host(glm_handle_t h, const void *X, const float *x_scale,
+                                   const uint8_t *y, const float *beta_host, int32_t K,
+                                   double *f_host, float *g_host, glm_stream_t stream);
+
+/*
+ * glm_logpost_grad_grouped — the hierarchical-Bayes batch of §4.1: group m
+ * owns rows [group_off[m], group_off[m+1]) of X and coefficient vector
+ * beta_m; its conditional log-posterior is L_m(beta_m) + log N(beta_m | mu,
+ * tau^2 I) with gradient g_L,m(beta_m) - (beta_m - mu) / tau^2.
+ *   group_off device, G+1 int64, non-decreasing, group_off[G] <= N
+ *   G         1 <= G
+ *   beta      device, G x P FP32;  mu device, P FP32;  tau > 0
+ *   f_out     device, G FP64;      g_out device, G x P FP32
+ * All groups are evaluated by one persistent launch over a (group, row-range)
+ * work list. Empty groups are allowed (their f is the prior alone).
+ * Deterministic. The handle's N bounds group_off[G].
+ */
+GLM_API glm_status_t glm_logpost_grad_grouped(glm_handle_t h, const void *X, const float *x_scale,
+                                      const uint8_t *y, const int64_t *group_off, int32_t G,
+                                      const float *beta, const float *mu, double tau,
+                                      double *f_out, float *g_out, glm_stream_t stream);
+
+/*
+ * glm_rwm_run — K independent random-walk Metropolis chains (the sampler of
+ * §2.2 that consumes the log-posterior), n_steps steps each, entirely on the
+ * device: step t proposes beta'_k = fmaf(step, z[t][k], beta_k) in FP32,
+ * evaluates f(beta'_k) with the fused kernel (one launch per step), and
+ * accepts iff log_u[t][k] < f(beta'_k) - f(beta_k), compared in FP64.
+ *   z          device, n_steps x K x P FP32 standard normals
+ *   log_u      device, n_steps x K FP64 logs of uniforms
+ *   beta_state device, K x P FP32 chain state, updated in place
+ *   f_state    device, K FP64 log-posterior at beta_state, updated in place;
+ *              computed first when init_f != 0
+ *   samples    device, n_steps x K x P FP32 or NULL (state after each step)
+ *   accept     device, n_steps x K bytes or NULL (1 = accepted)
+ *   logpost    device, n_steps x K FP64 or NULL (f after each step)
+ * 1 <= K <= min(k_max, 8). Asynchronous on `stream`.
+ */
+GLM_API glm_status_t glm_rwm_run(glm_handle_t h, const void *X, const float *x_scale,
+                         const uint8_t *y, int32_t K, int32_t n_steps, float step,
+                         const float *z, const double *log_u, float *beta_state,
+                         double *f_state, int32_t init_f, float *samples,
+                         uint8_t *accept, double *logpost, glm_stream_t stream);
+
+/*
+ * glm_quantize — convert a device FP32 matrix X32 (N x ld32, first P columns)
+ * to the handle's storage type in Xq (N x ld of that type, padding zero):
+ * GLM_X_BF16 rounds to nearest even; GLM_X_FP8E4M3 first sets
+ * x_scale[j] = the smallest power of two s with 448 s >= max_n |x_nj|
+ * (1 for an all-zero column) and stores the E4M3 code nearest to x_nj / s,
+ * ties to even, saturating. x_scale must be non-NULL exactly for FP8.
+ * Uses the handle's workspace; asynchronous on `stream`.
+ */
+GLM_API glm_status_t glm_quantize(glm_handle_t h, const float *X32, int32_t ld32, void *Xq,
+                          float *x_scale, glm_stream_t stream);
+
+/*
+ * glm_sync — synchronise `stream`, then read and clear the handle's
+ * device status word. Returns GLM_ERR_TIMEOUT if a bounded device wait
+ * expired since the last glm_sync (the outputs of that call are then NaN),
+ * GLM_ERR_CUDA on an asynchronous CUDA error, else GLM_OK.
+ */
+GLM_API glm_status_t glm_sync(glm_handle_t h, glm_stream_t stream);
+
+/*
+ * glm_selftest_wait_timeout — launch one CTA that waits on a shared-memory
+ * barrier nothing will ever complete, with a limit of `spin_limit` polls;
+ * when the limit runs out the kernel records GLM_ERR_TIMEOUT in the status
+ * word and returns. Exists so tests can check the bounded-wait path without
+ * faulting or hanging the GPU. Read the result with glm_sync.
+ */
+GLM_API glm_status_t glm_selftest_wait_timeout(glm_handle_t h, int32_t spin_limit,
+                                       glm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLM_H */

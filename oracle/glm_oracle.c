@@ -328,8 +328,9 @@ uint8_t oracle_e4m3_from_f64(double v)
     return e4m3_encode(v);
 }
 
-/* Smallest power of two s with 448 * s >= amax (s = 1 when amax == 0).
- * Every comparison is exact: 448 * 2^e is representable. */
+/* Smallest power of two s with 448 * s >= amax (s = 1 when amax == 0), but
+ * not below 2^-126 so that s is a normal FP32 number. Every comparison is
+ * exact: 448 * 2^e is representable. */
 double oracle_e4m3_column_scale(double amax)
 {
     if (!(amax > 0.0))
@@ -339,6 +340,8 @@ double oracle_e4m3_column_scale(double amax)
     int e = ex - 10;               /* 448 * 2^(ex-10) < 2^(ex-1) <= amax */
     while (448.0 * ldexp(1.0, e) < amax)
         ++e;
+    if (e < -126)                  /* keep the scale a normal FP32 number */
+        e = -126;
     return ldexp(1.0, e);
 }
 

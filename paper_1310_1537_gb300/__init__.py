@@ -1,0 +1,192 @@
+"""Python binding of the GB300 logistic-GLM library (libglm.so).
+
+Argument marshalling only: every function here has the name of a C entry
+point declared in include/glm.h and forwards device pointers (torch tensors'
+``data_ptr()``), sizes and the current CUDA stream to it. All arithmetic of
+the hot path runs in the library's CUDA kernels. There is no CPU fallback: if
+libglm.so cannot be built or loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libglm.so")
+
+GLM_OK = 0
+GLM_ERR_INVALID_ARG = 1
+GLM_ERR_UNSUPPORTED = 2
+GLM_ERR_OOM = 3
+GLM_ERR_CUDA = 4
+GLM_ERR_TIMEOUT = 5
+GLM_ERR_NO_DEVICE = 6
+
+GLM_X_F32 = 0
+GLM_X_BF16 = 1
+GLM_X_FP8E4M3 = 2
+
+GLM_FLAG_NO_TENSOR_CORES = 0x1
+
+ELEM_BYTES = {GLM_X_F32: 4, GLM_X_BF16: 2, GLM_X_FP8E4M3: 1}
+
+# Every C symbol the header declares (checked by the ABI test).
+EXPORTS = (
+    "glm_create", "glm_destroy", "glm_status_str", "glm_get_info", "glm_logpost_grad",
+    "glm_logpost_grad_host", "glm_logpost_grad_grouped", "glm_rwm_run", "glm_quantize",
+    "glm_sync", "glm_selftest_wait_timeout",
+)
+
+
+class GLMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {glm_status_str(status)} (status {status})")
+
+
+class glm_desc_t(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("p", C.c_int32), ("ld", C.c_int32),
+                ("k_max", C.c_int32), ("xtype", C.c_int32), ("prior_sigma", C.c_double),
+                ("device", C.c_int32), ("flags", C.c_uint32)]
+
+
+class glm_info_t(C.Structure):
+    _fields_ = [("sm_count", C.c_int32), ("grid", C.c_int32), ("tile_rows", C.c_int32),
+                ("stages", C.c_int32), ("smem_bytes", C.c_int32), ("tc_enabled", C.c_int32),
+                ("tc_min_k", C.c_int32), ("workspace_bytes", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(build_if_missing: bool = True):
+    """Load libglm.so (building it in-tree with nvcc when it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import build as _build
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; run paper_1310_1537_gb300.build")
+        lib = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        st = C.c_int
+        sig = {
+            "glm_create": ([C.POINTER(glm_desc_t), C.POINTER(vp)], st),
+            "glm_destroy": ([vp], st),
+            "glm_status_str": ([st], C.c_char_p),
+            "glm_get_info": ([vp, C.POINTER(glm_info_t)], st),
+            "glm_logpost_grad": ([vp, vp, vp, vp, vp, C.c_int32, vp, vp, vp], st),
+            "glm_logpost_grad_host": ([vp, vp, vp, vp, vp, C.c_int32, vp, vp, vp], st),
+            "glm_logpost_grad_grouped": ([vp, vp, vp, vp, vp, C.c_int32, vp, vp, C.c_double,
+                                          vp, vp, vp], st),
+            "glm_rwm_run": ([vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float, vp, vp, vp, vp,
+                             C.c_int32, vp, vp, vp, vp], st),
+            "glm_quantize": ([vp, vp, C.c_int32, vp, vp, vp], st),
+            "glm_sync": ([vp, vp], st),
+            "glm_selftest_wait_timeout": ([vp, C.c_int32, vp], st),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(status: int, where: str):
+    if status != GLM_OK:
+        raise GLMError(status, where)
+
+
+def glm_status_str(status: int) -> str:
+    return load().glm_status_str(int(status)).decode()
+
+
+def glm_create(n_rows: int, p: int, ld: int, k_max: int, xtype: int = GLM_X_F32,
+               prior_sigma: float = 10.0, device: int = 0, flags: int = 0) -> int:
+    d = glm_desc_t(int(n_rows), int(p), int(ld), int(k_max), int(xtype), float(prior_sigma),
+                   int(device), int(flags))
+    h = C.c_void_p()
+    _check(load().glm_create(C.byref(d), C.byref(h)), "glm_create")
+    return h.value
+
+
+def glm_destroy(h) -> None:
+    _check(load().glm_destroy(h), "glm_destroy")
+
+
+def glm_get_info(h) -> dict:
+    info = glm_info_t()
+    _check(load().glm_get_info(h, C.byref(info)), "glm_get_info")
+    return {k: getattr(info, k) for k, _ in glm_info_t._fields_}
+
+
+def glm_logpost_grad(h, X, x_scale, y, beta, K, f_out, g_out, stream=None) -> None:
+    _check(load().glm_logpost_grad(h, _ptr(X), _ptr(x_scale), _ptr(y), _ptr(beta), int(K),
+                                   _ptr(f_out), _ptr(g_out), _stream(stream)),
+           "glm_logpost_grad")
+
+
+def glm_logpost_grad_host(h, X, x_scale, y, beta_host, K, f_host, g_host, stream=None) -> None:
+    _check(load().glm_logpost_grad_host(h, _ptr(X), _ptr(x_scale), _ptr(y), _ptr(beta_host),
+                                        int(K), _ptr(f_host), _ptr(g_host), _stream(stream)),
+           "glm_logpost_grad_host")
+
+
+def glm_logpost_grad_grouped(h, X, x_scale, y, group_off, G, beta, mu, tau, f_out, g_out,
+                             stream=None) -> None:
+    _check(load().glm_logpost_grad_grouped(h, _ptr(X), _ptr(x_scale), _ptr(y), _ptr(group_off),
+                                           int(G), _ptr(beta), _ptr(mu), float(tau),
+                                           _ptr(f_out), _ptr(g_out), _stream(stream)),
+           "glm_logpost_grad_grouped")
+
+
+def glm_rwm_run(h, X, x_scale, y, K, n_steps, step, z, log_u, beta_state, f_state, init_f,
+                samples=None, accept=None, logpost=None, stream=None) -> None:
+    _check(load().glm_rwm_run(h, _ptr(X), _ptr(x_scale), _ptr(y), int(K), int(n_steps),
+                              C.c_float(step), _ptr(z), _ptr(log_u), _ptr(beta_state),
+                              _ptr(f_state), int(init_f), _ptr(samples), _ptr(accept),
+                              _ptr(logpost), _stream(stream)),
+           "glm_rwm_run")
+
+
+def glm_quantize(h, X32, ld32, Xq, x_scale=None, stream=None) -> None:
+    _check(load().glm_quantize(h, _ptr(X32), int(ld32), _ptr(Xq), _ptr(x_scale),
+                               _stream(stream)), "glm_quantize")
+
+
+def glm_sync(h, stream=None) -> int:
+    """Synchronise and return the status code (does not raise on TIMEOUT)."""
+    return int(load().glm_sync(h, _stream(stream)))
+
+
+def glm_selftest_wait_timeout(h, spin_limit, stream=None) -> None:
+    _check(load().glm_selftest_wait_timeout(h, int(spin_limit), _stream(stream)),
+           "glm_selftest_wait_timeout")

@@ -1,0 +1,228 @@
+// Internal declarations of the GB300 logistic-GLM library: the handle, the
+// kernel parameter blocks and the inline-PTX primitives (mbarrier, bulk TMA
+// copies) shared by the kernels. Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/glm.h"
+
+namespace glm {
+
+// Device status word bits (atomicOr'ed by kernels, read by glm_sync).
+constexpr unsigned kDevTimeout = 1u;
+
+// Poll limit of every mbarrier wait in the streaming kernels. One failed
+// try_wait suspends the thread for a bounded hardware interval, so this cap
+// is far above any legitimate wait yet ends in well under a minute.
+constexpr unsigned kSpinLimit = 1u << 24;
+
+constexpr int kFusedThreads = 256;
+constexpr int kMaxStages = 8;
+
+// ---------------------------------------------------------------------------
+// Kernel parameter block of the fused CUDA-core pass (glm_fused.cu).
+struct FusedParams {
+    const void *X;
+    const float *x_scale;      // FP8 column scales or nullptr
+    const uint8_t *y;
+    const float *beta;         // K x P (evaluation mode)
+    int64_t N;
+    int P;
+    int ld;
+    int K;                     // vectors in this launch (<= KC)
+    int stages;
+    int tile_rows;
+    double inv_s2;             // 1 / s^2
+    double prior_const;        // (P/2) log(2 pi s^2)
+    double *part;              // grid x KC x (P+1) per-CTA partials
+    unsigned *ticket;          // completion counter, returns to 0
+    unsigned *status;          // device status word
+    double *f_out;             // K (may be null in RWM mode)
+    float *g_out;              // K x P (may be null in RWM mode)
+    // random-walk Metropolis step (rwm != 0)
+    int rwm;
+    float step;
+    const float *z;            // K x P for this step
+    const double *log_u;       // K
+    float *state;              // K x P, updated by the last CTA
+    double *f_state;           // K
+    float *samples;            // K x P or null
+    uint8_t *accept;           // K or null
+    double *logpost;           // K or null
+};
+
+// Kernel parameter block of the grouped (hierarchical) pass.
+struct GroupedParams {
+    const void *X;
+    const float *x_scale;
+    const uint8_t *y;
+    const int64_t *off;        // G+1
+    const int *items;          // work list: 3 ints per item (group, row0, rows)
+    int n_items;
+    int G;
+    int P;
+    int ld;
+    const float *beta;         // G x P
+    const float *mu;           // P
+    double inv_t2;
+    double prior_const;
+    double *part;              // n_items x (P+1)
+    const int *item_first;     // G+1: items of group m are [item_first[m], item_first[m+1])
+    unsigned *group_ticket;    // G counters
+    unsigned *status;
+    double *f_out;
+    float *g_out;
+};
+
+}  // namespace glm
+
+// ---------------------------------------------------------------------------
+// The handle.
+struct glm_ctx {
+    glm_desc_t d;
+    int device;
+    int sm_count;
+    int elem_bytes;
+    // fused CUDA-core kernel configuration
+    int grid;
+    int tile_rows;
+    int split;
+    int stages;
+    int smem_bytes;
+    int kc_max;                 // largest KC instantiation usable for this xtype
+    // workspace
+    void *ws;                   // one device allocation
+    size_t ws_bytes;
+    double *part;               // per-CTA partials
+    size_t part_doubles;
+    unsigned *ticket;
+    unsigned *status;
+    float *scratch;             // quantiser / misc scratch (P floats)
+    // host-buffer entry point staging
+    float *beta_stage;          // device K_max x P
+    double *f_stage;            // device K_max
+    float *g_stage;             // device K_max x P
+    // tensor-core path
+    int tc_enabled;
+    int tc_min_k;
+    // grouped path work list (built per call shape, cached)
+    int *gr_items;
+    int gr_items_cap;
+    int *gr_item_first;
+    int gr_first_cap;
+    unsigned *gr_ticket;
+    int gr_ticket_cap;
+    double *gr_part;
+    size_t gr_part_cap;
+    int *gr_host_items;
+    int *gr_host_first;
+    int64_t *gr_host_off;
+};
+
+namespace glm {
+
+// Launchers implemented in the kernel translation units.
+glm_status_t launch_fused(glm_ctx *h, const FusedParams &p, int kc, cudaStream_t s);
+glm_status_t fused_configure(glm_ctx *h);
+glm_status_t launch_quantize(glm_ctx *h, const float *X32, int ld32, void *Xq, float *x_scale,
+                             cudaStream_t s);
+glm_status_t launch_wait_timeout(glm_ctx *h, int spin_limit, cudaStream_t s);
+
+}  // namespace glm
+
+// ---------------------------------------------------------------------------
+// Inline PTX primitives (device only).
+#ifdef __CUDACC__
+namespace glm {
+namespace ptx {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make mbarrier initialisation visible to the async proxy (TMA).
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned limit)
+{
+    for (unsigned i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
+// One-dimensional bulk copy global -> shared through the TMA engine,
+// completing `bytes` transactions on `bar`. dst, src 16-byte aligned; bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                         uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ double ld_cg_f64(const double *p)
+{
+    double v;
+    asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
+}  // namespace ptx
+}  // namespace glm
+#endif

@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads and exports every symbol include/glm.h declares.
+
+These tests make no compute call: they run on a machine without a GPU.
+"""
+import os
+import re
+
+import pytest
+
+import paper_1310_1537_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^GLM_API\s+[\w\s\*]+?\b(glm_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = pkg.load()
+    declared = _declared_symbols()
+    assert {"glm_create", "glm_logpost_grad", "glm_destroy"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(pkg.EXPORTS)
+
+
+def test_library_has_no_cuda_runtime_or_torch_dependency():
+    import subprocess
+    out = subprocess.run(["ldd", pkg.LIB_PATH], capture_output=True, text=True).stdout
+    assert "libcudart" not in out and "libtorch" not in out and "libc10" not in out
+
+
+def test_status_strings():
+    assert pkg.glm_status_str(0) == "ok"
+    assert pkg.glm_status_str(pkg.GLM_ERR_TIMEOUT) == "device wait timed out"
+    assert pkg.glm_status_str(99) == "unknown status"
+
+
+def test_create_rejects_bad_descriptors_without_touching_a_device():
+    import ctypes as C
+    lib = pkg.load()
+    h = C.c_void_p()
+    assert lib.glm_create(None, C.byref(h)) == pkg.GLM_ERR_INVALID_ARG
+    bad = [
+        dict(n_rows=-1, p=4, ld=4, k_max=1, xtype=0),
+        dict(n_rows=10, p=0, ld=4, k_max=1, xtype=0),
+        dict(n_rows=10, p=5, ld=4, k_max=1, xtype=0),      # ld < p
+        dict(n_rows=10, p=5, ld=5, k_max=1, xtype=0),      # 20-byte rows
+        dict(n_rows=10, p=5, ld=6, k_max=1, xtype=1),      # 12-byte rows
+        dict(n_rows=10, p=5, ld=8, k_max=1, xtype=2),      # 8-byte rows
+        dict(n_rows=10, p=4, ld=4, k_max=0, xtype=0),
+        dict(n_rows=10, p=4, ld=4, k_max=1, xtype=7),
+    ]
+    for b in bad:
+        d = pkg.glm_desc_t(b["n_rows"], b["p"], b["ld"], b["k_max"], b["xtype"], 10.0, 0, 0)
+        assert lib.glm_create(C.byref(d), C.byref(h)) == pkg.GLM_ERR_INVALID_ARG, b
+        assert h.value is None
+    d = pkg.glm_desc_t(10, 4, 4, 1, 0, -1.0, 0, 0)
+    assert lib.glm_create(C.byref(d), C.byref(h)) == pkg.GLM_ERR_INVALID_ARG
+
+
+def test_entry_points_reject_null_handle():
+    lib = pkg.load()
+    assert lib.glm_logpost_grad(None, None, None, None, None, 1, None, None, None) == 1
+    assert lib.glm_sync(None, None) == 1
+    assert lib.glm_destroy(None) == 0
+
+
+@pytest.mark.skipif(__import__("tests.conftest", fromlist=["gpu_available"]).gpu_available(),
+                    reason="checks the no-device path")
+def test_create_without_device_reports_no_device():
+    try:
+        pkg.glm_create(100, 4, 4, 1)
+    except pkg.GLMError as e:
+        assert e.status == pkg.GLM_ERR_NO_DEVICE
+    else:
+        pytest.fail("glm_create succeeded without a device")
