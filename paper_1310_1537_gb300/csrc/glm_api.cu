@@ -75,29 +75,49 @@ glm_status_t fused_configure(glm_ctx *h)
         return GLM_ERR_UNSUPPORTED;
     h->kc_max = (epc <= 8) ? 8 : 4;
     const int row_bytes = h->d.ld * es;
-    int split = pcu <= 32 ? 2 : (pcu <= 128 ? 4 : 32);
+    // Fewest threads per row whose one-batch tile still fits two stages:
+    // bigger tiles amortise the per-tile barriers and label loads.
+    int split = 32;
+    for (int cand = 1; cand <= 4; cand <<= 1) {
+        if (fused_smem_total(h, kFusedThreads / cand, 2, h->kc_max) <= kSmemOptin) {
+            split = cand;
+            break;
+        }
+    }
     const int fs = env_int("GLM_FUSED_SPLIT", 0);
     if (fs == 1 || fs == 2 || fs == 4 || fs == 32)
         split = fs;
+    int per_sm = env_int("GLM_FUSED_CTAS_PER_SM", 1);
+    if (per_sm < 1 || per_sm > 4)
+        per_sm = 1;
+    const int budget = kSmemOptin / per_sm - (per_sm > 1 ? 1024 : 0);
     int rb = kFusedThreads / split;
     int target = env_int("GLM_FUSED_STAGE_BYTES", 49152);
-    int T = (target / row_bytes) / rb * rb;
-    if (T < rb)
-        T = rb;
+    // rows per tile: a multiple of the phase-1 batch, at most four batches
+    auto pick_rows = [&](int rbv) {
+        int t = (target / row_bytes) / rbv * rbv;
+        if (t < rbv)
+            t = rbv;
+        if (t > 4 * rbv)
+            t = 4 * rbv;
+        return t;
+    };
+    int T = pick_rows(rb);
     const int ft = env_int("GLM_FUSED_TILE_ROWS", 0);
-    if (ft > 0)
+    if (ft > 0) {
         T = (ft + rb - 1) / rb * rb;
+        if (T > 4 * rb)
+            T = 4 * rb;
+    }
     int stages = kMaxStages;
-    while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max) > kSmemOptin)
+    while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max) > budget)
         --stages;
     if (stages < 2 && split != 32) {     // rows too wide: one warp per row, 8-row batches
         split = 32;
         rb = kFusedThreads / split;
-        T = (target / row_bytes) / rb * rb;
-        if (T < rb)
-            T = rb;
+        T = pick_rows(rb);
         stages = kMaxStages;
-        while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max) > kSmemOptin)
+        while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max) > budget)
             --stages;
     }
     if (stages < 2)
@@ -109,8 +129,8 @@ glm_status_t fused_configure(glm_ctx *h)
     h->stages = stages;
     h->tile_rows = T;
     h->smem_bytes = fused_smem_total(h, T, stages, h->kc_max);
-    const int per_sm = env_int("GLM_FUSED_CTAS_PER_SM", 1);
-    h->grid = h->sm_count * (per_sm >= 1 && per_sm <= 4 ? per_sm : 1);
+    h->grid = h->sm_count * per_sm;
+    h->use_pdl = env_int("GLM_NO_PDL", 0) ? 0 : 1;
     const int g = env_int("GLM_FUSED_GRID", 0);
     if (g > 0 && g <= 4096)
         h->grid = g;
@@ -173,7 +193,8 @@ static FusedParams base_params(const glm_ctx *h, const void *X, const float *x_s
     const double s2 = h->d.prior_sigma * h->d.prior_sigma;
     p.inv_s2 = 1.0 / s2;
     p.prior_const = 0.5 * (double)h->d.p * std::log(2.0 * M_PI * s2);
-    p.part = h->part;
+    p.acc = h->acc;
+    p.acc_flag = h->acc_flag;
     p.ticket = h->ticket;
     p.status = h->status;
     return p;
@@ -275,8 +296,9 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     h->tc_min_k = 16;
     h->tc_enabled = (!(d.flags & GLM_FLAG_NO_TENSOR_CORES)) && tc_supported(h) ? 1 : 0;
 
-    // Workspace: per-CTA partials, ticket, status, scratch, host-call staging.
-    const size_t part_doubles = (size_t)h->grid * 8 * (size_t)(d.p + 1);
+    // Workspace: fixed-point accumulators, ticket, flags, status, scratch,
+    // host-call staging (all zeroed once here; kernels return them to zero).
+    const size_t acc_words = (size_t)8 * (size_t)(d.p + 1) * fx::kLimbs;
     const size_t kp = (size_t)d.k_max * d.p;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -284,7 +306,8 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    const size_t o_part = take(part_doubles * 8);
+    const size_t o_acc = take(acc_words * 8);
+    const size_t o_flag = take(256);
     const size_t o_ticket = take(256);
     const size_t o_status = take(256);
     const size_t o_scratch = take((size_t)d.p * 4 + 256);
@@ -298,8 +321,8 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     }
     h->ws_bytes = off;
     uint8_t *base = static_cast<uint8_t *>(h->ws);
-    h->part = reinterpret_cast<double *>(base + o_part);
-    h->part_doubles = part_doubles;
+    h->acc = reinterpret_cast<unsigned long long *>(base + o_acc);
+    h->acc_flag = reinterpret_cast<unsigned *>(base + o_flag);
     h->ticket = reinterpret_cast<unsigned *>(base + o_ticket);
     h->status = reinterpret_cast<unsigned *>(base + o_status);
     h->scratch = reinterpret_cast<float *>(base + o_scratch);
@@ -421,6 +444,9 @@ glm_status_t glm_rwm_run(glm_handle_t h, const void *X, const float *x_scale, co
     const size_t kp = (size_t)K * h->d.p;
     for (int t = 0; t < n_steps; ++t) {
         FusedParams p = base_params(h, X, x_scale, y);
+        // after this call's first launch the previous kernel in the stream is
+        // one of ours, which never writes X or y: let it stream them early
+        p.early_prefetch = (t > 0 || init_f) ? 1 : 0;
         p.K = K;
         p.rwm = 1;
         p.step = step;

@@ -114,7 +114,7 @@ __device__ __forceinline__ void tr_map(float eta, float yv, float &ell, float &r
     float e = expf(-fabsf(eta));
     float sp = fmaxf(eta, 0.0f) + log1pf(e);
     ell = fmaf(yv, eta, -sp);
-    float inv = 1.0f / (1.0f + e);
+    float inv = __frcp_rn(1.0f + e);
     float sig = eta >= 0.0f ? inv : e * inv;
     r = yv - sig;
 }
@@ -165,35 +165,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
         s_failed = 0;
     }
 
-    // Coefficients (scaled by the FP8 column scales) into shared memory.
-    for (int idx = tid; idx < KC * PCE; idx += NT) {
-        const int k = idx / PCE;
-        const int j = idx - k * PCE;
-        float v = 0.0f;
-        if (k < p.K && j < P) {
-            const int64_t o = (int64_t)k * P + j;
-            v = p.rwm ? fmaf(p.step, p.z[o], p.state[o]) : p.beta[o];
-            if (p.x_scale)
-                v *= p.x_scale[j];
-        }
-        beta_s[idx] = v;
-    }
-    __syncthreads();
-
-    const uint64_t policy = ptx::policy_evict_first();
-    if (tid == 0) {
-        const int pre = ntiles < stages ? ntiles : stages;
-        for (int t = 0; t < pre; ++t) {
-            const int64_t row0 = r_begin + (int64_t)t * T;
-            const int rows = (int)((r_end - row0) < T ? (r_end - row0) : T);
-            const unsigned bytes = (unsigned)(rows * row_bytes);
-            ptx::mbar_arrive_expect_tx(&bars[t], bytes);
-            ptx::bulk_g2s(tiles + t * L.stage_bytes,
-                          static_cast<const uint8_t *>(p.X) + row0 * (int64_t)row_bytes, bytes,
-                          &bars[t], policy);
-        }
-    }
-
     // Phase-1 thread -> (row, split part) mapping.
     // SPLIT <= 4: 8 consecutive lanes take 8 consecutive rows of the same part
     // (a contiguous run of chunks), so a quarter-warp's 16-byte loads fall in
@@ -239,28 +210,95 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
     }
     bool failed = false;
 
+    // Labels are prefetched one tile ahead into registers (at most
+    // kMaxBatches phase-1 batches per tile) so their global-load latency
+    // overlaps the previous tile's work.
+    constexpr int kMaxBatches = 4;
+    float ycur[kMaxBatches], ynext[kMaxBatches];
+    auto load_y = [&](int tt, float *dst) {
+#pragma unroll
+        for (int bi = 0; bi < kMaxBatches; ++bi) {
+            dst[bi] = 0.0f;
+            if (tt < ntiles && h == 0) {
+                const int64_t r0 = r_begin + (int64_t)tt * T;
+                const int rws = (int)((r_end - r0) < T ? (r_end - r0) : T);
+                const int row = bi * RB + row_in_batch;
+                if (row < rws)
+                    dst[bi] = (float)__ldg(p.y + r0 + row);
+            }
+        }
+    };
+    // Prologue. X and y are never written by the previous launch of a
+    // Metropolis chain, so those launches may start streaming them before
+    // the programmatic dependency on the previous kernel resolves; every
+    // other read waits for it.
+    const uint64_t policy = ptx::policy_evict_first();
+    auto issue_prologue = [&]() {
+        if (tid != 0)
+            return;
+        const int pre = ntiles < stages ? ntiles : stages;
+        for (int t = 0; t < pre; ++t) {
+            const int64_t row0 = r_begin + (int64_t)t * T;
+            const int rows = (int)((r_end - row0) < T ? (r_end - row0) : T);
+            const unsigned bytes = (unsigned)(rows * row_bytes);
+            ptx::mbar_arrive_expect_tx(&bars[t], bytes);
+            ptx::bulk_g2s(tiles + t * L.stage_bytes,
+                          static_cast<const uint8_t *>(p.X) + row0 * (int64_t)row_bytes, bytes,
+                          &bars[t], policy);
+        }
+    };
+
+    if (p.early_prefetch) {
+        issue_prologue();
+        load_y(0, ycur);
+    }
+    ptx::grid_dep_wait();
+    if (!p.early_prefetch) {
+        issue_prologue();
+        load_y(0, ycur);
+    }
+    // Coefficients (scaled by the FP8 column scales) into shared memory.
+    for (int idx = tid; idx < KC * PCE; idx += NT) {
+        const int k = idx / PCE;
+        const int j = idx - k * PCE;
+        float v = 0.0f;
+        if (k < p.K && j < P) {
+            const int64_t o = (int64_t)k * P + j;
+            v = p.rwm ? fmaf(p.step, p.z[o], p.state[o]) : p.beta[o];
+            if (p.x_scale)
+                v *= p.x_scale[j];
+        }
+        beta_s[idx] = v;
+    }
+    __syncthreads();
+    ptx::grid_dep_launch_dependents();
+
     for (int t = 0; t < ntiles; ++t) {
         const int s = t % stages;
         const unsigned parity = (unsigned)(t / stages) & 1u;
         const int64_t row0 = r_begin + (int64_t)t * T;
         const int rows = (int)((r_end - row0) < T ? (r_end - row0) : T);
+        load_y(t + 1, ynext);
         const bool ok = ptx::mbar_wait_bounded(&bars[s], parity, kSpinLimit);
         const uint8_t *tile = tiles + s * L.stage_bytes;
 
         // ---- phase 1: eta, ell, r ------------------------------------------
-        for (int rb = 0; rb < rows; rb += RB) {
+#pragma unroll
+        for (int bi = 0; bi < kMaxBatches; ++bi) {
+            const int rb = bi * RB;
+            if (rb >= rows)
+                break;
             const int my_row = rb + row_in_batch;
             float acc[KC];
 #pragma unroll
             for (int k = 0; k < KC; ++k)
                 acc[k] = 0.0f;
             const bool valid = my_row < rows;
-            float yv = 0.0f;
-            if (valid && h == 0)
-                yv = (float)__ldg(p.y + row0 + my_row);
+            const float yv = ycur[bi];
             if (valid) {
                 const uint8_t *xr = tile + my_row * row_bytes;
                 int cs = rot;
+#pragma unroll 4
                 for (int it = 0; it < c_len; ++it) {
                     const int c = c_lo + cs * c_step;
                     cs = (cs + 1 == c_len) ? 0 : cs + 1;
@@ -324,6 +362,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
         // ---- phase 2: g += r x over the same tile ----------------------------
         if (q2 < G2) {
             const uint8_t *xc = tile + c2 * 16;
+#pragma unroll 4
             for (int i = q2; i < rows; i += G2) {
                 float xv[EPC];
                 TR::load(xc + i * row_bytes, xv);
@@ -358,6 +397,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
                           static_cast<const uint8_t *>(p.X) + nrow0 * (int64_t)row_bytes, bytes,
                           &bars[s], policy);
         }
+#pragma unroll
+        for (int bi = 0; bi < kMaxBatches; ++bi)
+            ycur[bi] = ynext[bi];
     }
 
     // ---- per-CTA partials ------------------------------------------------------
@@ -384,7 +426,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
     }
     __syncthreads();
     const bool bad = s_failed != 0;
-    double *mypart = p.part + (size_t)b * KC * (P + 1);
+    // Every CTA adds its partial sums into 128-bit fixed-point accumulators
+    // (integer adds are associative, so the totals do not depend on the order
+    // in which CTAs arrive: the result is bitwise reproducible).
     for (int idx = tid; idx < p.K * (P + 1); idx += NT) {
         const int k = idx / (P + 1);
         const int j = idx - k * (P + 1);
@@ -396,10 +440,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
             for (int q = 0; q < G2; ++q)
                 v += (double)red[(q * KC + k) * PCUE + (j - 1)];
         }
-        mypart[k * (P + 1) + j] = bad ? __longlong_as_double(0x7FF8000000000000LL) : v;
+        fx::add(p.acc + (size_t)idx * fx::kLimbs, bad ? __longlong_as_double(0x7FF8000000000000LL) : v,
+                p.acc_flag);
     }
 
-    // ---- last CTA: fixed-order cross-CTA reduction, prior, accept ----------------
+    // ---- last CTA: read the totals, add the prior, accept ----------------------
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -429,28 +474,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
             s_bb[k] = v;
     }
     __syncthreads();
+    const bool nan_out = __ldcg(p.acc_flag) != 0u;
     for (int idx = tid; idx < p.K * (P + 1); idx += NT) {
         const int k = idx / (P + 1);
         const int j = idx - k * (P + 1);
-        const double *src = p.part + (size_t)k * (P + 1) + j;
-        const size_t stride = (size_t)KC * (P + 1);
-        double v = 0.0;
-#pragma unroll 8
-        for (int c = 0; c < grid; ++c)
-            v += __ldcg(src + (size_t)c * stride);
+        unsigned long long *a = p.acc + (size_t)idx * fx::kLimbs;
+        double t = fx::read_and_clear(a);
+        if (nan_out)
+            t = __longlong_as_double(0x7FF8000000000000LL);
         if (j == 0) {
-            v += -0.5 * p.inv_s2 * s_bb[k] - p.prior_const;
-            s_f[k] = v;
+            const double v0 = t - 0.5 * p.inv_s2 * s_bb[k] - p.prior_const;
+            s_f[k] = v0;
             if (p.f_out)
-                p.f_out[k] = v;
+                p.f_out[k] = v0;
         } else {
             const int jj = j - 1;
             const int64_t o = (int64_t)k * P + jj;
             const float bj = p.rwm ? fmaf(p.step, p.z[o], p.state[o]) : p.beta[o];
             const double sc = p.x_scale ? (double)p.x_scale[jj] : 1.0;
-            const double gv = sc * v - (double)bj * p.inv_s2;
             if (p.g_out)
-                p.g_out[o] = (float)gv;
+                p.g_out[o] = (float)(sc * t - (double)bj * p.inv_s2);
         }
     }
     __syncthreads();
@@ -479,8 +522,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
                 p.samples[idx] = v;
         }
     }
-    if (tid == 0)
+    if (tid == 0) {
         *p.ticket = 0u;
+        *p.acc_flag = 0u;
+    }
 }
 
 // Host-side launch helper for one storage type.
@@ -505,8 +550,19 @@ glm_status_t launch_fused_t(glm_ctx *h, const FusedParams &prm, int kc, cudaStre
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) !=
         cudaSuccess)
         return GLM_ERR_CUDA;
-    fn<<<h->grid, kFusedThreads, L.total, s>>>(prm);
-    return cudaGetLastError() == cudaSuccess ? GLM_OK : GLM_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)h->grid);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.dynamicSmemBytes = (size_t)L.total;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = h->use_pdl ? 1 : 0;
+    if (cudaLaunchKernelEx(&cfg, fn, prm) != cudaSuccess)
+        return GLM_ERR_CUDA;
+    return GLM_OK;
 }
 
 }  // namespace glm

@@ -38,7 +38,8 @@ struct FusedParams {
     int tile_rows;
     double inv_s2;             // 1 / s^2
     double prior_const;        // (P/2) log(2 pi s^2)
-    double *part;              // grid x KC x (P+1) per-CTA partials
+    unsigned long long *acc;   // KC x (P+1) fixed-point accumulators (fx::kLimbs each), zero
+    unsigned *acc_flag;        // non-finite partial seen, returns to 0
     unsigned *ticket;          // completion counter, returns to 0
     unsigned *status;          // device status word
     double *f_out;             // K (may be null in RWM mode)
@@ -53,6 +54,7 @@ struct FusedParams {
     float *samples;            // K x P or null
     uint8_t *accept;           // K or null
     double *logpost;           // K or null
+    int early_prefetch;        // stream X/y before the launch dependency resolves
 };
 
 // Kernel parameter block of the grouped (hierarchical) pass.
@@ -94,11 +96,12 @@ struct glm_ctx {
     int stages;
     int smem_bytes;
     int kc_max;                 // largest KC instantiation usable for this xtype
+    int use_pdl;                // launch with programmatic stream serialization
     // workspace
     void *ws;                   // one device allocation
     size_t ws_bytes;
-    double *part;               // per-CTA partials
-    size_t part_doubles;
+    unsigned long long *acc;    // fixed-point cross-CTA accumulators
+    unsigned *acc_flag;
     unsigned *ticket;
     unsigned *status;
     float *scratch;             // quantiser / misc scratch (P floats)
@@ -216,6 +219,18 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     return pol;
 }
 
+// Programmatic dependent launch: wait for the previous kernel in the stream
+// (and the visibility of its writes) / allow the next one to start launching.
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_dep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ double ld_cg_f64(const double *p)
 {
     double v;
@@ -224,5 +239,62 @@ __device__ __forceinline__ double ld_cg_f64(const double *p)
 }
 
 }  // namespace ptx
+
+// Deterministic cross-CTA sums in 128-bit two's-complement fixed point with
+// 64 fractional bits. A value v is added as the integer floor(v * 2^64),
+// split into four 32-bit limbs, each accumulated in its own 64-bit word, so
+// no limb sum can overflow for fewer than 2^32 contributions and carries are
+// resolved only when the total is read. Integer addition is associative, so
+// the total is the same whatever order the CTAs arrive in. |v| must be below
+// 2^63; a non-finite or larger value raises the flag word instead.
+namespace fx {
+
+constexpr int kLimbs = 4;
+
+__device__ __forceinline__ void add(unsigned long long *acc, double v, unsigned *flag)
+{
+    if (v == 0.0)
+        return;
+    if (!isfinite(v) || fabs(v) >= 9.2e18) {
+        atomicOr(flag, 1u);
+        return;
+    }
+    int e;
+    const double m = frexp(v, &e);                            // v = m 2^e, 0.5 <= |m| < 1
+    const long long mi = (long long)ldexp(m, 53);             // exact: |mi| < 2^53
+    const int sh = e - 53 + 64;                               // v 2^64 = mi 2^sh
+    __int128 t;
+    if (sh >= 0)
+        t = (__int128)((unsigned __int128)(__int128)mi << sh); // sh <= 74: |t| < 2^127
+    else if (sh > -64)
+        t = (__int128)(mi >> (-sh));                          // arithmetic shift: floor
+    else
+        t = mi < 0 ? (__int128)-1 : (__int128)0;
+    const unsigned __int128 u = (unsigned __int128)t;
+#pragma unroll
+    for (int l = 0; l < kLimbs; ++l) {
+        const unsigned long long limb = (unsigned long long)((u >> (32 * l)) & 0xFFFFFFFFull);
+        if (limb)
+            atomicAdd(&acc[l], limb);
+    }
+}
+
+// Total of an accumulator (then reset to zero for the next launch).
+__device__ __forceinline__ double read_and_clear(unsigned long long *acc)
+{
+    unsigned __int128 T = 0;
+#pragma unroll
+    for (int l = 0; l < kLimbs; ++l) {
+        const unsigned long long w = __ldcg(acc + l);
+        T += (unsigned __int128)w << (32 * l);
+        acc[l] = 0ull;
+    }
+    const __int128 sv = (__int128)T;
+    const long long hi = (long long)(sv >> 64);               // integer part (floor)
+    const unsigned long long lo = (unsigned long long)sv;     // fraction * 2^64
+    return (double)hi + ldexp((double)lo, -64);
+}
+
+}  // namespace fx
 }  // namespace glm
 #endif
