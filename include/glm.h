@@ -218,6 +218,42 @@ GLM_API glm_status_t glm_sync(glm_handle_t h, glm_stream_t stream);
 GLM_API glm_status_t glm_selftest_wait_timeout(glm_handle_t h, int32_t spin_limit,
                                        glm_stream_t stream);
 
+/*
+ * glm_logpost_grad_noalloc — the same evaluation as glm_logpost_grad, for
+ * callers that cannot allocate device memory when they evaluate: code running
+ * under a memory pool or arena that owns all of the process's device memory,
+ * a real-time loop that must not take the allocator's locks or risk running
+ * out of memory mid-run, or a plugin whose host forbids allocation. The
+ * paper has no counterpart; this is a deployment convenience.
+ *
+ * There is no handle: the dataset shape is passed directly (n_rows, p, ld,
+ * xtype, prior_sigma as in glm_desc_t), and the call runs on the calling
+ * thread's current CUDA device, where all pointers must live. Arguments and
+ * results are as for glm_logpost_grad, with 1 <= K <= 1024.
+ *
+ * Memory. The call allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine. Its scratch (cross-CTA accumulators, completion ticket,
+ * flag words) is one fixed device array of about 263 KB inside this library,
+ * which every GPU that loads the library holds until the process exits. The
+ * array sizes the problem: p > 1024 returns GLM_ERR_INVALID_ARG.
+ *
+ * Sharing. Every call on a device uses the same array, which keeps what the
+ * last call left; each call clears it on its stream before launching. Calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads on one device, without ordering between them) race on the array
+ * and give wrong results: order them on one stream.
+ *
+ * Set-up. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. A bounded device wait that expires shows up as
+ * NaN results.
+ */
+GLM_API glm_status_t glm_logpost_grad_noalloc(const void *X, const float *x_scale,
+                                              const uint8_t *y, int64_t n_rows, int32_t p,
+                                              int32_t ld, int32_t xtype, double prior_sigma,
+                                              const float *beta, int32_t K, double *f_out,
+                                              float *g_out, glm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ ELEM_BYTES = {GLM_X_F32: 4, GLM_X_BF16: 2, GLM_X_FP8E4M3: 1}
 EXPORTS = (
     "glm_create", "glm_destroy", "glm_status_str", "glm_get_info", "glm_logpost_grad",
     "glm_logpost_grad_host", "glm_logpost_grad_grouped", "glm_rwm_run", "glm_quantize",
-    "glm_sync", "glm_selftest_wait_timeout",
+    "glm_sync", "glm_selftest_wait_timeout", "glm_logpost_grad_noalloc",
 )
 
 
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
             "glm_quantize": ([vp, vp, C.c_int32, vp, vp, vp], st),
             "glm_sync": ([vp, vp], st),
             "glm_selftest_wait_timeout": ([vp, C.c_int32, vp], st),
+            "glm_logpost_grad_noalloc": ([vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                          C.c_double, vp, C.c_int32, vp, vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -190,3 +192,12 @@ def glm_sync(h, stream=None) -> int:
 def glm_selftest_wait_timeout(h, spin_limit, stream=None) -> None:
     _check(load().glm_selftest_wait_timeout(h, int(spin_limit), _stream(stream)),
            "glm_selftest_wait_timeout")
+
+
+def glm_logpost_grad_noalloc(X, x_scale, y, n_rows, p, ld, xtype, prior_sigma, beta, K, f_out,
+                             g_out, stream=None) -> None:
+    """Handle-free evaluation that allocates no device memory (fixed scratch)."""
+    _check(load().glm_logpost_grad_noalloc(_ptr(X), _ptr(x_scale), _ptr(y), int(n_rows), int(p),
+                                           int(ld), int(xtype), float(prior_sigma), _ptr(beta),
+                                           int(K), _ptr(f_out), _ptr(g_out), _stream(stream)),
+           "glm_logpost_grad_noalloc")
