@@ -321,8 +321,9 @@ def run_ours(args, world, rank, local):
             "hbm_gbs": achieved,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profile_traffic(),
+                         "traffic_source": "profiles/fused_f32_big.md (ncu dram bytes, one launch)",
                          "peak_kind": f"{peak_kind} hbm_gbs", "kernel":
-                             "fused_logpost_grad_kernel<F32Tag,1,2>",
+                             "glm::fused_logpost_grad_kernel<F32Tag, 1, 1>",
                          "algorithmic_bytes_per_launch": bytes_step,
                          "kernel_ms": kern_ms,
                          "kernel_ms_def": "timed region / launches (launches overlap by "
