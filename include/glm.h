@@ -82,6 +82,7 @@ typedef struct {
     double prior_sigma;   /* s > 0 of the N(0, s^2 I) prior                   */
     int32_t device;       /* CUDA device ordinal                              */
     uint32_t flags;       /* GLM_FLAG_* below                                 */
+    int32_t g_max;        /* largest G of any grouped call (0: none)          */
 } glm_desc_t;
 
 /* Never route K > 1 evaluations to the tensor-core kernel. */
@@ -153,18 +154,42 @@ GLM_API glm_status_t glm_logpost_grad_host(glm_handle_t h, const void *X, const 
  * owns rows [group_off[m], group_off[m+1]) of X and coefficient vector
  * beta_m; its conditional log-posterior is L_m(beta_m) + log N(beta_m | mu,
  * tau^2 I) with gradient g_L,m(beta_m) - (beta_m - mu) / tau^2.
- *   group_off device, G+1 int64, non-decreasing, group_off[G] <= N
- *   G         1 <= G
+ *   group_off device, G+1 int64, non-decreasing, group_off[G] <= N (the
+ *             handle's n_rows); rows before group_off[0] are not read
+ *   G         1 <= G <= the handle's g_max
  *   beta      device, G x P FP32;  mu device, P FP32;  tau > 0
  *   f_out     device, G FP64;      g_out device, G x P FP32
- * All groups are evaluated by one persistent launch over a (group, row-range)
- * work list. Empty groups are allowed (their f is the prior alone).
- * Deterministic. The handle's N bounds group_off[G].
+ * One persistent launch evaluates every group: the rows
+ * [group_off[0], group_off[G]) are split evenly over all warps of the grid,
+ * each warp streams its rows once through its own TMA ring and keeps one
+ * group's sums in registers until the group ends; per-group sums meet in
+ * fixed-point accumulators and the last warp to contribute to a group adds
+ * the prior and writes its f and g. Empty groups are allowed (their f is the
+ * prior alone). Deterministic. Malformed offsets (decreasing, or beyond N)
+ * give undefined results; they are not checked on the host because the
+ * offsets live in device memory.
  */
 GLM_API glm_status_t glm_logpost_grad_grouped(glm_handle_t h, const void *X, const float *x_scale,
                                       const uint8_t *y, const int64_t *group_off, int32_t G,
                                       const float *beta, const float *mu, double tau,
                                       double *f_out, float *g_out, glm_stream_t stream);
+
+/*
+ * glm_autotune_grouped — choose the grouped pass's launch shape for this
+ * handle by measurement: every feasible combination of kernel variant (row
+ * streamed once per lane with shuffles, or register-resident narrow rows for
+ * at most 32 used columns), warps per CTA, rows per TMA slot, slots per warp
+ * ring and CTAs per SM is run `reps` times (1..1000) on the given inputs and
+ * timed with CUDA events; the fastest is kept in the handle and used by later
+ * glm_logpost_grad_grouped calls. Arguments as for glm_logpost_grad_grouped;
+ * f_out and g_out receive a valid result. Synchronises `stream` and creates
+ * CUDA events: call it outside stream capture, not on a latency-critical path.
+ */
+GLM_API glm_status_t glm_autotune_grouped(glm_handle_t h, const void *X, const float *x_scale,
+                                          const uint8_t *y, const int64_t *group_off, int32_t G,
+                                          const float *beta, const float *mu, double tau,
+                                          double *f_out, float *g_out, int32_t reps,
+                                          glm_stream_t stream);
 
 /*
  * glm_rwm_run — K independent random-walk Metropolis chains (the sampler of

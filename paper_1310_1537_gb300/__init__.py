@@ -36,6 +36,7 @@ EXPORTS = (
     "glm_create", "glm_destroy", "glm_status_str", "glm_get_info", "glm_logpost_grad",
     "glm_logpost_grad_host", "glm_logpost_grad_grouped", "glm_rwm_run", "glm_quantize",
     "glm_sync", "glm_selftest_wait_timeout", "glm_logpost_grad_noalloc",
+    "glm_autotune_grouped",
 )
 
 
@@ -48,7 +49,7 @@ class GLMError(RuntimeError):
 class glm_desc_t(C.Structure):
     _fields_ = [("n_rows", C.c_int64), ("p", C.c_int32), ("ld", C.c_int32),
                 ("k_max", C.c_int32), ("xtype", C.c_int32), ("prior_sigma", C.c_double),
-                ("device", C.c_int32), ("flags", C.c_uint32)]
+                ("device", C.c_int32), ("flags", C.c_uint32), ("g_max", C.c_int32)]
 
 
 class glm_info_t(C.Structure):
@@ -91,6 +92,8 @@ def load(build_if_missing: bool = True):
             "glm_selftest_wait_timeout": ([vp, C.c_int32, vp], st),
             "glm_logpost_grad_noalloc": ([vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
                                           C.c_double, vp, C.c_int32, vp, vp, vp], st),
+            "glm_autotune_grouped": ([vp, vp, vp, vp, vp, C.c_int32, vp, vp, C.c_double, vp, vp,
+                                      C.c_int32, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -132,9 +135,9 @@ def glm_status_str(status: int) -> str:
 
 
 def glm_create(n_rows: int, p: int, ld: int, k_max: int, xtype: int = GLM_X_F32,
-               prior_sigma: float = 10.0, device: int = 0, flags: int = 0) -> int:
+               prior_sigma: float = 10.0, device: int = 0, flags: int = 0, g_max: int = 0) -> int:
     d = glm_desc_t(int(n_rows), int(p), int(ld), int(k_max), int(xtype), float(prior_sigma),
-                   int(device), int(flags))
+                   int(device), int(flags), int(g_max))
     h = C.c_void_p()
     _check(load().glm_create(C.byref(d), C.byref(h)), "glm_create")
     return h.value
@@ -168,6 +171,14 @@ def glm_logpost_grad_grouped(h, X, x_scale, y, group_off, G, beta, mu, tau, f_ou
                                            int(G), _ptr(beta), _ptr(mu), float(tau),
                                            _ptr(f_out), _ptr(g_out), _stream(stream)),
            "glm_logpost_grad_grouped")
+
+
+def glm_autotune_grouped(h, X, x_scale, y, group_off, G, beta, mu, tau, f_out, g_out, reps=5,
+                         stream=None) -> None:
+    _check(load().glm_autotune_grouped(h, _ptr(X), _ptr(x_scale), _ptr(y), _ptr(group_off),
+                                       int(G), _ptr(beta), _ptr(mu), float(tau), _ptr(f_out),
+                                       _ptr(g_out), int(reps), _stream(stream)),
+           "glm_autotune_grouped")
 
 
 def glm_rwm_run(h, X, x_scale, y, K, n_steps, step, z, log_u, beta_state, f_state, init_f,

@@ -16,9 +16,6 @@ glm_status_t launch_fused_fp8(glm_ctx *h, const FusedParams &p, int kc, cudaStre
 glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
                        const float *beta, int K, double *f_out, float *g_out, cudaStream_t s);
 bool tc_supported(const glm_ctx *h);
-glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
-                            const int64_t *group_off, int G, const float *beta, const float *mu,
-                            double tau, double *f_out, float *g_out, cudaStream_t s);
 
 static int elem_bytes_of(int xtype)
 {
@@ -261,7 +258,7 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     if (es == 0 || d.n_rows < 0 || d.p < 1 || d.ld < d.p || d.k_max < 1 || d.k_max > 1024 ||
         !(d.prior_sigma > 0.0) || !std::isfinite(d.prior_sigma) || d.device < 0)
         return GLM_ERR_INVALID_ARG;
-    if (((int64_t)d.ld * es) % 16 != 0)
+    if (((int64_t)d.ld * es) % 16 != 0 || d.g_max < 0)
         return GLM_ERR_INVALID_ARG;
     if (d.n_rows > ((int64_t)1 << 40) || (int64_t)d.ld * es > (1 << 20))
         return GLM_ERR_UNSUPPORTED;
@@ -293,6 +290,8 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
         delete h;
         return st;
     }
+    if (d.g_max > 0 && grouped_configure(h) != GLM_OK)
+        h->gr_warps = 0;   // rows too wide for the grouped kernel: grouped calls are unsupported
     h->tc_min_k = 16;
     h->tc_enabled = (!(d.flags & GLM_FLAG_NO_TENSOR_CORES)) && tc_supported(h) ? 1 : 0;
 
@@ -314,6 +313,10 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     const size_t o_bst = take(kp * 4);
     const size_t o_fst = take((size_t)d.k_max * 8);
     const size_t o_gst = take(kp * 4);
+    const size_t gmax = (size_t)(d.g_max > 0 ? d.g_max : 0);
+    const size_t o_gacc = take(gmax * (size_t)(d.p + 1) * fx::kLimbs * 8);
+    const size_t o_gtk = take(gmax * 4);
+    const size_t o_gfl = take(gmax * 4);
     if (cudaMalloc(&h->ws, off) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -329,6 +332,11 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     h->beta_stage = reinterpret_cast<float *>(base + o_bst);
     h->f_stage = reinterpret_cast<double *>(base + o_fst);
     h->g_stage = reinterpret_cast<float *>(base + o_gst);
+    if (gmax) {
+        h->gr_acc = reinterpret_cast<unsigned long long *>(base + o_gacc);
+        h->gr_ticket = reinterpret_cast<unsigned *>(base + o_gtk);
+        h->gr_flag = reinterpret_cast<unsigned *>(base + o_gfl);
+    }
     if (cudaMemset(h->ws, 0, off) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(h->ws);
         delete h;
@@ -345,13 +353,6 @@ glm_status_t glm_destroy(glm_handle_t h)
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     cudaFree(h->ws);
-    cudaFree(h->gr_items);
-    cudaFree(h->gr_item_first);
-    cudaFree(h->gr_ticket);
-    cudaFree(h->gr_part);
-    std::free(h->gr_host_items);
-    std::free(h->gr_host_first);
-    std::free(h->gr_host_off);
     delete h;
     return GLM_OK;
 }
@@ -474,11 +475,29 @@ glm_status_t glm_logpost_grad_grouped(glm_handle_t h, const void *X, const float
     glm_status_t st = check_x_args(h, X, x_scale, y);
     if (st != GLM_OK)
         return st;
-    if (G < 1 || !group_off || !beta || !mu || !f_out || !g_out || !(tau > 0.0) ||
-        !std::isfinite(tau) || !aligned(group_off, 8) || !aligned(f_out, 8))
+    if (G < 1 || G > h->d.g_max || !group_off || !beta || !mu || !f_out || !g_out ||
+        !(tau > 0.0) || !std::isfinite(tau) || !aligned(group_off, 8) || !aligned(f_out, 8) ||
+        !aligned(beta, 4) || !aligned(mu, 4) || !aligned(g_out, 4))
         return GLM_ERR_INVALID_ARG;
     return launch_grouped(h, X, x_scale, y, group_off, G, beta, mu, tau, f_out, g_out,
                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+glm_status_t glm_autotune_grouped(glm_handle_t h, const void *X, const float *x_scale,
+                                  const uint8_t *y, const int64_t *group_off, int32_t G,
+                                  const float *beta, const float *mu, double tau, double *f_out,
+                                  float *g_out, int32_t reps, glm_stream_t stream)
+{
+    if (!h)
+        return GLM_ERR_INVALID_ARG;
+    glm_status_t st = check_x_args(h, X, x_scale, y);
+    if (st != GLM_OK)
+        return st;
+    if (G < 1 || G > h->d.g_max || !group_off || !beta || !mu || !f_out || !g_out ||
+        !(tau > 0.0) || !std::isfinite(tau) || reps < 1 || reps > 1000)
+        return GLM_ERR_INVALID_ARG;
+    return autotune_grouped(h, X, x_scale, y, group_off, G, beta, mu, tau, f_out, g_out,
+                            reinterpret_cast<cudaStream_t>(stream), reps);
 }
 
 glm_status_t glm_quantize(glm_handle_t h, const float *X32, int32_t ld32, void *Xq,

@@ -57,27 +57,28 @@ struct FusedParams {
     int early_prefetch;        // stream X/y before the launch dependency resolves
 };
 
-// Kernel parameter block of the grouped (hierarchical) pass.
+// Kernel parameter block of the grouped (hierarchical-Bayes) pass.
 struct GroupedParams {
     const void *X;
-    const float *x_scale;
+    const float *x_scale;      // FP8 column scales or nullptr
     const uint8_t *y;
-    const int64_t *off;        // G+1
-    const int *items;          // work list: 3 ints per item (group, row0, rows)
-    int n_items;
+    const int64_t *off;        // G+1 row offsets
+    int64_t N;                 // rows of X (bound on the offsets)
     int G;
     int P;
     int ld;
+    int stages;                // slots per warp ring
+    int units;                 // 32-row units per slot (narrow-row kernel)
     const float *beta;         // G x P
     const float *mu;           // P
-    double inv_t2;
-    double prior_const;
-    double *part;              // n_items x (P+1)
-    const int *item_first;     // G+1: items of group m are [item_first[m], item_first[m+1])
-    unsigned *group_ticket;    // G counters
+    double inv_t2;             // 1 / tau^2
+    double prior_const;        // (P/2) log(2 pi tau^2)
+    unsigned long long *acc;   // G x (P+1) fixed-point accumulators, zero
+    unsigned *gticket;         // G completion counters, zero
+    unsigned *gflag;           // G non-finite flags, zero
     unsigned *status;
-    double *f_out;
-    float *g_out;
+    double *f_out;             // G
+    float *g_out;              // G x P
 };
 
 }  // namespace glm
@@ -112,18 +113,15 @@ struct glm_ctx {
     // tensor-core path
     int tc_enabled;
     int tc_min_k;
-    // grouped path work list (built per call shape, cached)
-    int *gr_items;
-    int gr_items_cap;
-    int *gr_item_first;
-    int gr_first_cap;
+    // grouped (hierarchical) path: per-group accumulators, sized by g_max
+    unsigned long long *gr_acc;
     unsigned *gr_ticket;
-    int gr_ticket_cap;
-    double *gr_part;
-    size_t gr_part_cap;
-    int *gr_host_items;
-    int *gr_host_first;
-    int64_t *gr_host_off;
+    unsigned *gr_flag;
+    int gr_warps;               // warps per CTA
+    int gr_stages;              // slots per warp ring
+    int gr_units;               // 32-row units per slot
+    int gr_narrow;              // 1: register-resident narrow-row kernel
+    int gr_grid;
 };
 
 namespace glm {
@@ -134,6 +132,13 @@ glm_status_t fused_configure(glm_ctx *h);
 glm_status_t launch_quantize(glm_ctx *h, const float *X32, int ld32, void *Xq, float *x_scale,
                              cudaStream_t s);
 glm_status_t launch_wait_timeout(glm_ctx *h, int spin_limit, cudaStream_t s);
+glm_status_t grouped_configure(glm_ctx *h);
+glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
+                            const int64_t *group_off, int G, const float *beta, const float *mu,
+                            double tau, double *f_out, float *g_out, cudaStream_t s);
+glm_status_t autotune_grouped(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
+                              const int64_t *group_off, int G, const float *beta, const float *mu,
+                              double tau, double *f_out, float *g_out, cudaStream_t s, int reps);
 
 }  // namespace glm
 
