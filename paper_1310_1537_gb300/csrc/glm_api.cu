@@ -317,6 +317,8 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     const size_t o_gacc = take(gmax * (size_t)(d.p + 1) * fx::kLimbs * 8);
     const size_t o_gtk = take(gmax * 4);
     const size_t o_gfl = take(gmax * 4);
+    const size_t tcb = h->tc_enabled ? tc_workspace_bytes(h) : 0;
+    const size_t o_tc = take(tcb);
     if (cudaMalloc(&h->ws, off) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -332,6 +334,12 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     h->beta_stage = reinterpret_cast<float *>(base + o_bst);
     h->f_stage = reinterpret_cast<double *>(base + o_fst);
     h->g_stage = reinterpret_cast<float *>(base + o_gst);
+    if (tcb) {
+        const int MBt = (d.p + 127) / 128;
+        h->tc_part_f = reinterpret_cast<double *>(base + o_tc);
+        h->tc_part_g = reinterpret_cast<float *>(base + o_tc + (size_t)h->sm_count * 64 * 8);
+        (void)MBt;
+    }
     if (gmax) {
         h->gr_acc = reinterpret_cast<unsigned long long *>(base + o_gacc);
         h->gr_ticket = reinterpret_cast<unsigned *>(base + o_gtk);

@@ -113,6 +113,10 @@ struct glm_ctx {
     // tensor-core path
     int tc_enabled;
     int tc_min_k;
+    alignas(64) unsigned char tc_map[128];   // CUtensorMap of the last X seen
+    const void *tc_map_ptr;
+    double *tc_part_f;          // per-CTA f partials
+    float *tc_part_g;           // per-CTA g partials
     // grouped (hierarchical) path: per-group accumulators, sized by g_max
     unsigned long long *gr_acc;
     unsigned *gr_ticket;
@@ -133,6 +137,7 @@ glm_status_t launch_quantize(glm_ctx *h, const float *X32, int ld32, void *Xq, f
                              cudaStream_t s);
 glm_status_t launch_wait_timeout(glm_ctx *h, int spin_limit, cudaStream_t s);
 glm_status_t grouped_configure(glm_ctx *h);
+size_t tc_workspace_bytes(const glm_ctx *h);
 glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
                             const int64_t *group_off, int G, const float *beta, const float *mu,
                             double tau, double *f_out, float *g_out, cudaStream_t s);

@@ -1,14 +1,641 @@
-// Tensor-core (tcgen05) batched pass: not built yet.
+// Batched log-posterior + gradient on the tcgen05 tensor cores.
+//
+// With K coefficient vectors the two LA maps of the paper's gradient routine
+// (§4.2: X beta, then X^t g_f) become real contractions, N x P x K each. One
+// persistent CTA per SM streams 128-row tiles of X (BF16) into shared memory
+// with TMA (128B swizzle) and, from the same staged tile,
+//   MMA1: D1[128 x 2K] = X_tile[128 x P] . [beta_hi | beta_lo]^T   (A K-major)
+//   epilogue (8 warps, one row per thread): eta = D1_hi + D1_lo, the TR map
+//            (ell, r), f accumulated per thread; r split into bf16 hi + lo
+//            and written to shared memory as R_tile[128 x 2K]
+//   MMA2: D2[P x 2K] += X_tile^T . R_tile                (both operands MN-major)
+// D1 is double-buffered in tensor memory so MMA1 of the next tile overlaps the
+// epilogue; D2 stays in tensor memory for the CTA's whole run (the gradient
+// never leaves the SM until the end). Splitting beta and r into two bf16 terms
+// keeps about 16 significant bits, so the products match the FP32 path to
+// ~1e-5 while X stays in its 2-byte storage. Per-CTA partials are combined by
+// a second kernel in a fixed order (deterministic).
+//
+// Warp roles: warp 0 issues TMA loads, warp 1 allocates tensor memory and one
+// of its threads issues the MMAs, warps 2..9 run the epilogue. Every wait is
+// bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
 #include "glm_internal.cuh"
 
 namespace glm {
 
-bool tc_supported(const glm_ctx *) { return false; }
+constexpr int kTcRows = 128;
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
+constexpr int kTcMaxStages = 4;
+constexpr int kTcMaxP = 256;
+constexpr int kTcMaxKB = 64;
+constexpr int kTcTmemCols = 512;
 
-glm_status_t launch_tc(glm_ctx *, const void *, const float *, const uint8_t *, const float *, int,
-                       double *, float *, cudaStream_t)
+struct TcParams {
+    const uint8_t *y;
+    const float *beta;          // kk x P, this chunk
+    int64_t N;
+    int P;
+    int kk;                     // vectors in this chunk (<= KB)
+    int PA;                     // 64-column atoms of the tile
+    int MB;                     // 128-column blocks of P for MMA2
+    int stages;
+    double *part_f;             // grid x KB
+    float *part_g;              // grid x KB x (MB*128)
+    unsigned *status;
+};
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t sw128(int r, int c_elem16)
 {
-    return GLM_ERR_UNSUPPORTED;
+    // byte offset of 16-bit element (r, c) in a [rows x 64] region, 128B swizzle
+    const uint32_t chunk = (uint32_t)c_elem16 >> 3;
+    return (uint32_t)r * 128u + ((chunk ^ ((uint32_t)r & 7u)) << 4) + (((uint32_t)c_elem16 & 7u) << 1);
+}
+
+__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;            // descriptor version for tcgen05
+    d |= 2ull << 61;            // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, M=128, N=n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, int a_mn, int b_mn)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     ptx::smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(ptx::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(ptx::smem_u32(bar))
+        : "memory");
+}
+
+// 32 lanes x N columns of 32-bit values from tensor memory (N = 8, 16 or 32).
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float *v);
+
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// TR map with the fast hardware exp/log/reciprocal; overflow-free forms.
+__device__ __forceinline__ void tr_fast(float eta, float yv, float &ell, float &r)
+{
+    const float e = __expf(-fabsf(eta));
+    const float sp = fmaxf(eta, 0.0f) + __logf(1.0f + e);
+    ell = fmaf(yv, eta, -sp);
+    const float inv = __fdividef(1.0f, 1.0f + e);
+    r = yv - (eta >= 0.0f ? inv : e * inv);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1)
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+    return v;
+}
+
+}  // namespace tc
+
+// Shared-memory layout of the tensor-core kernel (1024-byte aligned parts).
+struct TcLayout {
+    int x_stage;    // PA * 16 KB
+    int x_off;
+    int b1_off;     // PA regions of (2KB rows x 128 B)
+    int r_off;      // ceil(2KB/64) regions of (128 rows x 128 B)
+    int bar_off;
+    int sf_off;     // 4 x KB doubles (inside the R tile, used after the last MMA)
+    int total;      // including 1 KB alignment slack
+};
+
+__host__ __device__ inline TcLayout tc_layout(int PA, int KB, int stages)
+{
+    TcLayout L;
+    const int N1 = 2 * KB;
+    L.x_stage = PA * 16384;
+    L.x_off = 0;
+    L.b1_off = stages * L.x_stage;
+    L.r_off = L.b1_off + PA * N1 * 128;
+    const int nr = (N1 + 63) / 64;
+    L.bar_off = L.r_off + nr * 16384;
+    L.sf_off = L.r_off;         // reuses the R tile once every MMA has completed
+    L.total = L.bar_off + 256 + 1024;
+    return L;
+}
+
+template <int KB>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_logpost_grad_kernel(const __grid_constant__ CUtensorMap tmap, TcParams p)
+{
+    constexpr int N1 = 2 * KB;
+    constexpr int KH = KB / 2;                 // vectors per epilogue warp
+    constexpr uint32_t ID1 = tc::idesc_bf16(N1, 0, 0);
+    constexpr uint32_t ID2 = tc::idesc_bf16(N1, 1, 1);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int PA = p.PA;
+    const int MB = p.MB;
+    const int stages = p.stages;
+    const TcLayout L = tc_layout(PA, KB, stages);
+    uint8_t *xs = smem + L.x_off;
+    uint8_t *b1 = smem + L.b1_off;
+    uint8_t *rb = smem + L.r_off;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bar_off);
+    uint64_t *x_full = bars;                    // [stages]
+    uint64_t *x_empty = bars + kTcMaxStages;    // [stages]
+    uint64_t *d1_full = bars + 2 * kTcMaxStages;
+    uint64_t *d1_empty = d1_full + 2;
+    uint64_t *r_full = d1_empty + 2;
+    uint64_t *r_empty = r_full + 1;
+    uint64_t *d2_done = r_empty + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d2_done + 1);
+    double *sf = reinterpret_cast<double *>(smem + L.sf_off);
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int grid = gridDim.x;
+    const int b = blockIdx.x;
+    const int64_t ntiles_all = (p.N + kTcRows - 1) / kTcRows;
+    const int nt = (int)(ntiles_all > b ? (ntiles_all - b + grid - 1) / grid : 0);
+
+    if (tid == 0) {
+        for (int s = 0; s < kTcMaxStages; ++s) {
+            ptx::mbar_init(&x_full[s], 1);
+            ptx::mbar_init(&x_empty[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&d1_full[i], 1);
+            ptx::mbar_init(&d1_empty[i], kTcEpiWarps);
+        }
+        ptx::mbar_init(r_full, kTcEpiWarps);
+        ptx::mbar_init(r_empty, 1);
+        ptx::mbar_init(d2_done, 1);
+        ptx::fence_mbar_init();
+        s_abort = 0;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         ptx::smem_u32(tmem_slot)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    ptx::grid_dep_wait();
+    // beta split into two bf16 terms, K-major 128B-swizzled B operand:
+    // rows n < KB hold beta_hi of vector n, rows KB + n hold beta_lo.
+    for (int idx = tid; idx < N1 * PA * 64; idx += kTcThreads) {
+        const int n = idx / (PA * 64);
+        const int col = idx - n * (PA * 64);
+        const int k = n < KB ? n : n - KB;
+        float v = 0.0f;
+        if (k < p.kk && col < p.P)
+            v = p.beta[(size_t)k * p.P + col];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 val = n < KB ? hi : __float2bfloat16_rn(v - __bfloat162float(hi));
+        *reinterpret_cast<__nv_bfloat16 *>(b1 + (col >> 6) * (N1 * 128) + tc::sw128(n, col & 63)) = val;
+    }
+    ptx::fence_proxy_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+    ptx::grid_dep_launch_dependents();
+
+    if (warp == 0) {
+        // ---- TMA producer ------------------------------------------------------------
+        if (lane == 0) {
+            const unsigned bytes = (unsigned)(PA * 16384);
+            for (int i = 0; i < nt; ++i) {
+                const int s = i % stages;
+                const int use = i / stages;
+                if (use > 0 && !ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
+                    atomicOr(p.status, kDevTimeout);
+                    s_abort = 1;
+                    break;
+                }
+                const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kTcRows);
+                ptx::mbar_arrive_expect_tx(&x_full[s], bytes);
+                for (int a = 0; a < PA; ++a)
+                    tc::tma_load_2d(xs + s * L.x_stage + a * 16384, &tmap, a * 64, row0, &x_full[s]);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----------------------------------------------------------------
+        if (lane == 0) {
+            const uint32_t xs_a = ptx::smem_u32(xs);
+            const uint32_t b1_a = ptx::smem_u32(b1);
+            const uint32_t rb_a = ptx::smem_u32(rb);
+            bool ok = true;
+            for (int i = 0; i <= nt && ok; ++i) {
+                if (i < nt) {
+                    const int s = i % stages;
+                    const int bb = i & 1;
+                    ok = ptx::mbar_wait_bounded(&x_full[s], (unsigned)(i / stages) & 1u, kSpinLimit);
+                    if (ok && i >= 2)
+                        ok = ptx::mbar_wait_bounded(&d1_empty[bb], (unsigned)((i >> 1) - 1) & 1u,
+                                                    kSpinLimit);
+                    if (!ok)
+                        break;
+                    tc::fence_after();
+                    const uint32_t xa = xs_a + s * L.x_stage;
+                    for (int ks = 0; ks < PA * 4; ++ks) {
+                        const uint64_t ad = tc::mdesc(xa + (ks >> 2) * 16384 + (ks & 3) * 32, 16, 1024);
+                        const uint64_t bd =
+                            tc::mdesc(b1_a + (ks >> 2) * (N1 * 128) + (ks & 3) * 32, 16, 1024);
+                        tc::mma(tmem + bb * N1, ad, bd, ID1, ks > 0 ? 1u : 0u);
+                    }
+                    tc::commit(&d1_full[bb]);
+                }
+                if (i >= 1) {
+                    const int j = i - 1;
+                    const int sj = j % stages;
+                    ok = ptx::mbar_wait_bounded(r_full, (unsigned)j & 1u, kSpinLimit);
+                    if (!ok)
+                        break;
+                    tc::fence_after();
+                    const uint32_t xa = xs_a + sj * L.x_stage;
+                    for (int mb = 0; mb < MB; ++mb) {
+                        for (int ks = 0; ks < kTcRows / 16; ++ks) {
+                            const uint64_t ad = tc::mdesc(xa + (2 * mb) * 16384 + ks * 16 * 128, 16384, 1024);
+                            const uint64_t bd = tc::mdesc(rb_a + ks * 16 * 128, 16384, 1024);
+                            tc::mma(tmem + (2 + mb) * N1, ad, bd, ID2, (j > 0 || ks > 0) ? 1u : 0u);
+                        }
+                    }
+                    tc::commit(&x_empty[sj]);
+                    tc::commit(r_empty);
+                }
+            }
+            if (!ok) {
+                atomicOr(p.status, kDevTimeout);
+                s_abort = 1;
+            }
+            if (nt > 0)
+                tc::commit(d2_done);
+        }
+    } else {
+        // ---- epilogue: one row per thread, KH vectors per warp --------------------------
+        const int q = warp & 3;                 // tensor-memory lane quarter
+        const int hh = (warp - 2) >> 2;         // which half of the vectors
+        const int row = q * 32 + lane;
+        float facc[KH];
+#pragma unroll
+        for (int k = 0; k < KH; ++k)
+            facc[k] = 0.0f;
+        auto load_y = [&](int i) -> float {
+            if (i >= nt)
+                return 0.0f;
+            const int64_t r = (int64_t)(b + (int64_t)i * grid) * kTcRows + row;
+            return r < p.N ? (float)__ldg(p.y + r) : 0.0f;
+        };
+        float ycur = load_y(0);
+        bool ok = true;
+        for (int i = 0; i < nt; ++i) {
+            const int bb = i & 1;
+            const float ynext = load_y(i + 1);
+            if (!ptx::mbar_wait_bounded(&d1_full[bb], (unsigned)(i >> 1) & 1u, kSpinLimit)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after();
+            float dh[KH], dl[KH];
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + bb * N1 + hh * KH;
+            tc::tmem_ld<KH>(ta, dh);
+            tc::tmem_ld<KH>(ta + KB, dl);
+            tc::tmem_wait_ld();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0)
+                ptx::mbar_arrive(&d1_empty[bb]);
+            const bool valid = (int64_t)(b + (int64_t)i * grid) * kTcRows + row < p.N;
+            uint32_t rh[KH / 2], rl[KH / 2];
+#pragma unroll
+            for (int k = 0; k < KH; k += 2) {
+                float ell0, r0, ell1, r1;
+                tc::tr_fast(dh[k] + dl[k], ycur, ell0, r0);
+                tc::tr_fast(dh[k + 1] + dl[k + 1], ycur, ell1, r1);
+                if (valid) {
+                    facc[k] += ell0;
+                    facc[k + 1] += ell1;
+                } else {
+                    r0 = 0.0f;
+                    r1 = 0.0f;
+                }
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0, r1);
+                const float2 hf = __bfloat1622float2(h2);
+                rh[k / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+                rl[k / 2] = tc::pack_bf16(r0 - hf.x, r1 - hf.y);
+            }
+            if (i >= 1 && !ptx::mbar_wait_bounded(r_empty, (unsigned)(i - 1) & 1u, kSpinLimit)) {
+                ok = false;
+                break;
+            }
+            // R tile row `row`: columns n = hh*KH + k (hi) and KB + hh*KH + k (lo)
+#pragma unroll
+            for (int c = 0; c < KH / 8; ++c) {
+                const int nh = hh * KH + c * 8;
+                const int nl = KB + hh * KH + c * 8;
+                uint4 vh = make_uint4(rh[c * 4], rh[c * 4 + 1], rh[c * 4 + 2], rh[c * 4 + 3]);
+                uint4 vl = make_uint4(rl[c * 4], rl[c * 4 + 1], rl[c * 4 + 2], rl[c * 4 + 3]);
+                *reinterpret_cast<uint4 *>(rb + (nh >> 6) * 16384 + tc::sw128(row, nh & 63)) = vh;
+                *reinterpret_cast<uint4 *>(rb + (nl >> 6) * 16384 + tc::sw128(row, nl & 63)) = vl;
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0)
+                ptx::mbar_arrive(r_full);
+            ycur = ynext;
+        }
+        if (!ok) {
+            atomicOr(p.status, kDevTimeout);
+            s_abort = 1;
+        }
+        // g partial: D2 blocks, lane = column p of X, KH vectors per warp
+        const int PP = MB * 128;
+        bool have = nt > 0 && ok && ptx::mbar_wait_bounded(d2_done, 0u, kSpinLimit);
+        if (nt > 0 && !have) {
+            atomicOr(p.status, kDevTimeout);
+            s_abort = 1;
+        }
+        tc::fence_after();
+        // f partial of this CTA: rows of the warp, then the four lane quarters in
+        // order (the buffer lies in the R tile, idle now that every MMA is done)
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
+#pragma unroll
+        for (int k = 0; k < KH; ++k) {
+            const double v = tc::warp_sum((double)facc[k]);
+            if (lane == 0)
+                sf[q * KB + hh * KH + k] = v;
+        }
+        for (int mb = 0; mb < MB; ++mb) {
+            float gh[KH], gl[KH];
+            if (have) {
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (2 + mb) * N1 + hh * KH;
+                tc::tmem_ld<KH>(ta, gh);
+                tc::tmem_ld<KH>(ta + KB, gl);
+                tc::tmem_wait_ld();
+            }
+            const int pcol = mb * 128 + q * 32 + lane;
+#pragma unroll
+            for (int k = 0; k < KH; ++k) {
+                const float g = have ? gh[k] + gl[k] : 0.0f;
+                p.part_g[((size_t)b * KB + hh * KH + k) * PP + pcol] = g;
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
+        const int et = tid - 64;
+        if (et < KB) {
+            const double v = sf[et] + sf[KB + et] + sf[2 * KB + et] + sf[3 * KB + et];
+            p.part_f[(size_t)b * KB + et] = s_abort ? __longlong_as_double(0x7FF8000000000000LL) : v;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTcTmemCols)
+                     : "memory");
+}
+
+// Fixed-order combine of the per-CTA partials, plus the Gaussian prior.
+__global__ void tc_reduce_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g,
+                                 int parts, int KB, int PP, int P, int kk,
+                                 const float *__restrict__ beta, const float *__restrict__ x_scale,
+                                 double inv_s2, double prior_const, double *__restrict__ f_out,
+                                 float *__restrict__ g_out)
+{
+    ptx::grid_dep_wait();
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= kk * (P + 1))
+        return;
+    const int k = idx / (P + 1);
+    const int j = idx - k * (P + 1);
+    if (j == 0) {
+        double v = 0.0;
+        for (int c = 0; c < parts; ++c)
+            v += part_f[(size_t)c * KB + k];
+        double bb = 0.0;
+        for (int t = 0; t < P; ++t) {
+            const double bt = (double)beta[(size_t)k * P + t];
+            bb += bt * bt;
+        }
+        f_out[k] = v - 0.5 * inv_s2 * bb - prior_const;
+    } else {
+        const int jj = j - 1;
+        double v = 0.0;
+        for (int c = 0; c < parts; ++c)
+            v += (double)part_g[((size_t)c * KB + k) * PP + jj];
+        const double sc = x_scale ? (double)x_scale[jj] : 1.0;
+        g_out[(size_t)k * P + jj] = (float)(sc * v - (double)beta[(size_t)k * P + jj] * inv_s2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+bool tc_supported(const glm_ctx *h)
+{
+    return h->d.xtype == GLM_X_BF16 && h->d.p <= kTcMaxP && h->d.k_max >= 16 &&
+           std::getenv("GLM_NO_TC") == nullptr;
+}
+
+static int tc_stages(int PA, int KB)
+{
+    int st = kTcMaxStages;
+    while (st >= 2 && tc_layout(PA, KB, st).total > 232448)
+        --st;
+    return st;
+}
+
+static glm_status_t tc_tensor_map(glm_ctx *h, const void *X)
+{
+    if (h->tc_map_ptr == X)
+        return GLM_OK;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return GLM_ERR_CUDA;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld, (cuuint64_t)h->d.n_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)kTcRows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap *map = reinterpret_cast<CUtensorMap *>(h->tc_map);
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(X), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return GLM_ERR_CUDA;
+    h->tc_map_ptr = X;
+    return GLM_OK;
+}
+
+size_t tc_workspace_bytes(const glm_ctx *h)
+{
+    const int MB = (h->d.p + 127) / 128;
+    return (size_t)h->sm_count * kTcMaxKB * 8 + (size_t)h->sm_count * kTcMaxKB * MB * 128 * 4 + 256;
+}
+
+glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
+                       const float *beta, int K, double *f_out, float *g_out, cudaStream_t s)
+{
+    if (!h->tc_part_f || h->d.n_rows > ((int64_t)1 << 31) - kTcRows)
+        return GLM_ERR_UNSUPPORTED;
+    glm_status_t st = tc_tensor_map(h, X);
+    if (st != GLM_OK)
+        return st;
+    const int P = h->d.p;
+    const int PA = (P + 63) / 64;
+    const int MB = (P + 127) / 128;
+    const double s2 = h->d.prior_sigma * h->d.prior_sigma;
+    const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(h->tc_map);
+    for (int k0 = 0; k0 < K; k0 += kTcMaxKB) {
+        const int kk = (K - k0) < kTcMaxKB ? (K - k0) : kTcMaxKB;
+        const int KB = kk <= 16 ? 16 : (kk <= 32 ? 32 : 64);
+        TcParams prm;
+        std::memset(&prm, 0, sizeof(prm));
+        prm.y = y;
+        prm.beta = beta + (size_t)k0 * P;
+        prm.N = h->d.n_rows;
+        prm.P = P;
+        prm.kk = kk;
+        prm.PA = PA;
+        prm.MB = MB;
+        prm.stages = tc_stages(PA, KB);
+        if (prm.stages < 2)
+            return GLM_ERR_UNSUPPORTED;
+        prm.part_f = h->tc_part_f;
+        prm.part_g = h->tc_part_g;
+        prm.status = h->status;
+        auto fn = KB == 16 ? &tc_logpost_grad_kernel<16>
+                           : (KB == 32 ? &tc_logpost_grad_kernel<32> : &tc_logpost_grad_kernel<64>);
+        const TcLayout L = tc_layout(PA, KB, prm.stages);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) !=
+            cudaSuccess)
+            return GLM_ERR_CUDA;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)h->sm_count);
+        cfg.blockDim = dim3(kTcThreads);
+        cfg.dynamicSmemBytes = (size_t)L.total;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, fn, *map, prm) != cudaSuccess)
+            return GLM_ERR_CUDA;
+        const int nout = kk * (P + 1);
+        cudaLaunchConfig_t rc = {};
+        rc.gridDim = dim3((unsigned)((nout + 255) / 256));
+        rc.blockDim = dim3(256);
+        rc.stream = s;
+        rc.attrs = attr;
+        rc.numAttrs = 1;
+        if (cudaLaunchKernelEx(&rc, tc_reduce_kernel, (const double *)h->tc_part_f,
+                               (const float *)h->tc_part_g, h->sm_count, KB, MB * 128, P, kk,
+                               beta + (size_t)k0 * P, x_scale, 1.0 / s2,
+                               0.5 * (double)P * std::log(2.0 * M_PI * s2), f_out + k0,
+                               g_out + (size_t)k0 * P) != cudaSuccess)
+            return GLM_ERR_CUDA;
+    }
+    return GLM_OK;
 }
 
 }  // namespace glm
