@@ -489,36 +489,59 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // Fixed-order combine of the per-CTA partials, plus the Gaussian prior.
+// Blocks [0, ng) produce g: one thread per (vector, column), loads batched so
+// that 16 are in flight before they are added in CTA order. The remaining
+// blocks produce f: one warp per vector, lanes over CTAs and over columns of
+// beta, finished by an exact butterfly.
 __global__ void tc_reduce_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g,
-                                 int parts, int KB, int PP, int P, int kk,
+                                 int parts, int KB, int PP, int P, int kk, int ng,
                                  const float *__restrict__ beta, const float *__restrict__ x_scale,
                                  double inv_s2, double prior_const, double *__restrict__ f_out,
                                  float *__restrict__ g_out)
 {
     ptx::grid_dep_wait();
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= kk * (P + 1))
-        return;
-    const int k = idx / (P + 1);
-    const int j = idx - k * (P + 1);
-    if (j == 0) {
+    if ((int)blockIdx.x < ng) {
+        const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+        if (idx >= kk * P)
+            return;
+        const int k = idx / P;
+        const int jj = idx - k * P;
+        const float *src = part_g + (size_t)k * PP + jj;
+        const size_t stride = (size_t)KB * PP;
         double v = 0.0;
-        for (int c = 0; c < parts; ++c)
-            v += part_f[(size_t)c * KB + k];
-        double bb = 0.0;
-        for (int t = 0; t < P; ++t) {
-            const double bt = (double)beta[(size_t)k * P + t];
-            bb += bt * bt;
+        for (int c0 = 0; c0 < parts; c0 += 16) {
+            float buf[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                buf[u] = (c0 + u < parts) ? __ldg(src + (size_t)(c0 + u) * stride) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                v += (double)buf[u];
         }
-        f_out[k] = v - 0.5 * inv_s2 * bb - prior_const;
-    } else {
-        const int jj = j - 1;
-        double v = 0.0;
-        for (int c = 0; c < parts; ++c)
-            v += (double)part_g[((size_t)c * KB + k) * PP + jj];
         const double sc = x_scale ? (double)x_scale[jj] : 1.0;
         g_out[(size_t)k * P + jj] = (float)(sc * v - (double)beta[(size_t)k * P + jj] * inv_s2);
+        return;
     }
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int k = ((int)blockIdx.x - ng) * (blockDim.x >> 5) + warp;
+    if (k >= kk)
+        return;
+    double v = 0.0;
+    for (int c = lane; c < parts; c += 32)
+        v += part_f[(size_t)c * KB + k];
+    double bb = 0.0;
+    for (int t = lane; t < P; t += 32) {
+        const double bt = (double)beta[(size_t)k * P + t];
+        bb += bt * bt;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+        bb += __shfl_xor_sync(0xFFFFFFFFu, bb, m);
+    }
+    if (lane == 0)
+        f_out[k] = v - 0.5 * inv_s2 * bb - prior_const;
 }
 
 // ---------------------------------------------------------------------------
@@ -621,15 +644,16 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         cfg.numAttrs = 1;
         if (cudaLaunchKernelEx(&cfg, fn, *map, prm) != cudaSuccess)
             return GLM_ERR_CUDA;
-        const int nout = kk * (P + 1);
+        const int ng = (kk * P + 255) / 256;
+        const int nf = (kk + 7) / 8;
         cudaLaunchConfig_t rc = {};
-        rc.gridDim = dim3((unsigned)((nout + 255) / 256));
+        rc.gridDim = dim3((unsigned)(ng + nf));
         rc.blockDim = dim3(256);
         rc.stream = s;
         rc.attrs = attr;
         rc.numAttrs = 1;
         if (cudaLaunchKernelEx(&rc, tc_reduce_kernel, (const double *)h->tc_part_f,
-                               (const float *)h->tc_part_g, h->sm_count, KB, MB * 128, P, kk,
+                               (const float *)h->tc_part_g, h->sm_count, KB, MB * 128, P, kk, ng,
                                beta + (size_t)k0 * P, x_scale, 1.0 / s2,
                                0.5 * (double)P * std::log(2.0 * M_PI * s2), f_out + k0,
                                g_out + (size_t)k0 * P) != cudaSuccess)
