@@ -3,22 +3,24 @@
 // With K coefficient vectors the two LA maps of the paper's gradient routine
 // (§4.2: X beta, then X^t g_f) become real contractions, N x P x K each. One
 // persistent CTA per SM streams 128-row tiles of X (BF16) into shared memory
-// with TMA (128B swizzle) and, from the same staged tile,
-//   MMA1: D1[128 x 2K] = X_tile[128 x P] . [beta_hi | beta_lo]^T   (A K-major)
-//   epilogue (8 warps, one row per thread): eta = D1_hi + D1_lo, the TR map
-//            (ell, r), f accumulated per thread; r split into bf16 hi + lo
-//            and written to shared memory as R_tile[128 x 2K]
-//   MMA2: D2[P x 2K] += X_tile^T . R_tile                (both operands MN-major)
-// D1 is double-buffered in tensor memory so MMA1 of the next tile overlaps the
-// epilogue; D2 stays in tensor memory for the CTA's whole run (the gradient
-// never leaves the SM until the end). Splitting beta and r into two bf16 terms
-// keeps about 16 significant bits, so the products match the FP32 path to
-// ~1e-5 while X stays in its 2-byte storage. Per-CTA partials are combined by
-// a second kernel in a fixed order (deterministic).
+// with TMA (128B swizzle, 2-4 stages) and, from the same staged tile,
+//   MMA1: D1[2K x 128] = B1 . X_tile^T   (A = B1 in tensor memory: rows 2k and
+//         2k+1 hold the bf16 hi and lo parts of beta_k; B = the tile, K-major)
+//   epilogue (8 warps): lane n of D1 belongs to vector k = n/2; the two lanes
+//         of a vector add their hi and lo products (one shuffle) to get eta
+//         for 64 rows, each takes 32 of them through the TR map (ell, r),
+//         accumulates f, splits r into bf16 hi + lo and writes them to the
+//         R tile in shared memory
+//   MMA2: D2[P x 2K] += X_tile^T . R_tile   (both operands MN-major)
+// D2 stays in tensor memory for the CTA's whole run: the gradient never
+// leaves the SM until the end. Splitting beta and r into two bf16 terms keeps
+// about 16 significant bits, so the results match the FP32 path to ~1e-5
+// while X stays in 2-byte storage. Per-CTA partials are combined by a second
+// kernel in a fixed order (deterministic).
 //
 // Warp roles: warp 0 issues TMA loads, warp 1 allocates tensor memory and one
-// of its threads issues the MMAs, warps 2..9 run the epilogue. Every wait is
-// bounded.
+// of its threads issues the MMAs, warps 2..9 run the epilogue (and first load
+// beta into tensor memory). Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cmath>
@@ -30,7 +32,10 @@
 namespace glm {
 
 constexpr int kTcRows = 128;
-constexpr int kTcEpiWarps = 8;
+constexpr int kTcEpiWarps = 16;
+constexpr int kTcEpiGroups = kTcEpiWarps / 4;       // warps per tensor-memory lane quarter
+constexpr int kTcEpiCols = 128 / kTcEpiGroups;      // D1 columns (tile rows) per warp
+constexpr int kTcEpiRows = kTcEpiCols / 2;          // rows per thread
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTcMaxStages = 4;
 constexpr int kTcMaxP = 256;
@@ -46,8 +51,9 @@ struct TcParams {
     int PA;                     // 64-column atoms of the tile
     int MB;                     // 128-column blocks of P for MMA2
     int stages;
-    double *part_f;             // grid x KB
-    float *part_g;              // grid x KB x (MB*128)
+    int y_al4;                  // y is 4-byte aligned: labels read as words
+    double *part_f;             // grid x 64
+    float *part_g;              // grid x 64 x (MB*128)
     unsigned *status;
 };
 
@@ -158,13 +164,39 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float *v)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+        "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// MMA with the A operand in tensor memory.
+__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
 // TR map with the fast hardware exp/log/reciprocal; overflow-free forms.
 __device__ __forceinline__ void tr_fast(float eta, float yv, float &ell, float &r)
 {
-    const float e = __expf(-fabsf(eta));
-    const float sp = fmaxf(eta, 0.0f) + __logf(1.0f + e);
-    ell = fmaf(yv, eta, -sp);
-    const float inv = __fdividef(1.0f, 1.0f + e);
+    const float e = __expf(-fabsf(eta));                  // exp(-|eta|) in (0, 1]
+    const float d = 1.0f + e;
+    ell = fmaf(yv, eta, -fmaxf(eta, 0.0f));               // y eta - max(eta, 0)
+    ell = fmaf(-0.69314718055994531f, __log2f(d), ell);   // - log(1 + exp(-|eta|))
+    const float inv = __fdividef(1.0f, d);
     r = yv - (eta >= 0.0f ? inv : e * inv);
 }
 
@@ -188,52 +220,50 @@ __device__ __forceinline__ double warp_sum(double v)
 struct TcLayout {
     int x_stage;    // PA * 16 KB
     int x_off;
-    int b1_off;     // PA regions of (2KB rows x 128 B)
-    int r_off;      // ceil(2KB/64) regions of (128 rows x 128 B)
+    int r_off;      // R tile: 2 regions of (128 rows x 128 B)
     int bar_off;
-    int sf_off;     // 4 x KB doubles (inside the R tile, used after the last MMA)
+    int sf_off;     // 4 x 64 doubles (inside the R tile, used after the last MMA)
     int total;      // including 1 KB alignment slack
 };
 
-__host__ __device__ inline TcLayout tc_layout(int PA, int KB, int stages)
+__host__ __device__ inline TcLayout tc_layout(int PA, int stages)
 {
     TcLayout L;
-    const int N1 = 2 * KB;
     L.x_stage = PA * 16384;
     L.x_off = 0;
-    L.b1_off = stages * L.x_stage;
-    L.r_off = L.b1_off + PA * N1 * 128;
-    const int nr = (N1 + 63) / 64;
-    L.bar_off = L.r_off + nr * 16384;
-    L.sf_off = L.r_off;         // reuses the R tile once every MMA has completed
+    L.r_off = stages * L.x_stage;
+    L.bar_off = L.r_off + 2 * 16384;
+    L.sf_off = L.r_off;
     L.total = L.bar_off + 256 + 1024;
     return L;
 }
 
-template <int KB>
+// Tensor-memory columns: beta (A operand of MMA1) at 0, D1 at 128, D2 block
+// mb at 256 + 128 mb.
+constexpr int kTcB1Col = 0;
+constexpr int kTcD1Col = 128;
+constexpr int kTcD2Col = 256;
+
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_logpost_grad_kernel(const __grid_constant__ CUtensorMap tmap, TcParams p)
 {
-    constexpr int N1 = 2 * KB;
-    constexpr int KH = KB / 2;                 // vectors per epilogue warp
-    constexpr uint32_t ID1 = tc::idesc_bf16(N1, 0, 0);
-    constexpr uint32_t ID2 = tc::idesc_bf16(N1, 1, 1);
+    constexpr uint32_t ID1 = tc::idesc_bf16(128, 0, 0);
+    constexpr uint32_t ID2 = tc::idesc_bf16(128, 1, 1);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int PA = p.PA;
     const int MB = p.MB;
     const int stages = p.stages;
-    const TcLayout L = tc_layout(PA, KB, stages);
+    const TcLayout L = tc_layout(PA, stages);
     uint8_t *xs = smem + L.x_off;
-    uint8_t *b1 = smem + L.b1_off;
     uint8_t *rb = smem + L.r_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bar_off);
     uint64_t *x_full = bars;                    // [stages]
     uint64_t *x_empty = bars + kTcMaxStages;    // [stages]
     uint64_t *d1_full = bars + 2 * kTcMaxStages;
-    uint64_t *d1_empty = d1_full + 2;
-    uint64_t *r_full = d1_empty + 2;
+    uint64_t *d1_empty = d1_full + 1;
+    uint64_t *r_full = d1_empty + 1;
     uint64_t *r_empty = r_full + 1;
     uint64_t *d2_done = r_empty + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d2_done + 1);
@@ -253,10 +283,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ptx::mbar_init(&x_full[s], 1);
             ptx::mbar_init(&x_empty[s], 1);
         }
-        for (int i = 0; i < 2; ++i) {
-            ptx::mbar_init(&d1_full[i], 1);
-            ptx::mbar_init(&d1_empty[i], kTcEpiWarps);
-        }
+        ptx::mbar_init(d1_full, 1);
+        ptx::mbar_init(d1_empty, kTcEpiWarps);
         ptx::mbar_init(r_full, kTcEpiWarps);
         ptx::mbar_init(r_empty, 1);
         ptx::mbar_init(d2_done, 1);
@@ -272,24 +300,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     ptx::grid_dep_wait();
-    // beta split into two bf16 terms, K-major 128B-swizzled B operand:
-    // rows n < KB hold beta_hi of vector n, rows KB + n hold beta_lo.
-    for (int idx = tid; idx < N1 * PA * 64; idx += kTcThreads) {
-        const int n = idx / (PA * 64);
-        const int col = idx - n * (PA * 64);
-        const int k = n < KB ? n : n - KB;
-        float v = 0.0f;
-        if (k < p.kk && col < p.P)
-            v = p.beta[(size_t)k * p.P + col];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 val = n < KB ? hi : __float2bfloat16_rn(v - __bfloat162float(hi));
-        *reinterpret_cast<__nv_bfloat16 *>(b1 + (col >> 6) * (N1 * 128) + tc::sw128(n, col & 63)) = val;
-    }
-    ptx::fence_proxy_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
+
+    // beta into tensor memory: lane n = 2k + part holds the bf16 hi (part 0) or
+    // lo (part 1) term of beta_k, two columns of beta per 32-bit cell
+    if (warp >= 2 && warp < 6) {
+        const int q = warp & 3;
+        const int n = q * 32 + lane;
+        const int k = n >> 1;
+        const int part = n & 1;
+        for (int cb = 0; cb < PA * 32; cb += 32) {
+            uint32_t r[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                float v2[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int col = 2 * (cb + j) + e;
+                    float v = 0.0f;
+                    if (k < p.kk && col < p.P)
+                        v = p.beta[(size_t)k * p.P + col];
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                    v2[e] = part ? v - __bfloat162float(hi) : v;
+                }
+                r[j] = tc::pack_bf16(v2[0], v2[1]);
+            }
+            tc::tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + kTcB1Col + cb, r);
+        }
+        tc::tmem_wait_st();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
     ptx::grid_dep_launch_dependents();
 
     if (warp == 0) {
@@ -314,28 +359,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ---- MMA issuer ----------------------------------------------------------------
         if (lane == 0) {
             const uint32_t xs_a = ptx::smem_u32(xs);
-            const uint32_t b1_a = ptx::smem_u32(b1);
             const uint32_t rb_a = ptx::smem_u32(rb);
             bool ok = true;
             for (int i = 0; i <= nt && ok; ++i) {
                 if (i < nt) {
                     const int s = i % stages;
-                    const int bb = i & 1;
                     ok = ptx::mbar_wait_bounded(&x_full[s], (unsigned)(i / stages) & 1u, kSpinLimit);
-                    if (ok && i >= 2)
-                        ok = ptx::mbar_wait_bounded(&d1_empty[bb], (unsigned)((i >> 1) - 1) & 1u,
-                                                    kSpinLimit);
+                    if (ok && i >= 1)
+                        ok = ptx::mbar_wait_bounded(d1_empty, (unsigned)(i - 1) & 1u, kSpinLimit);
                     if (!ok)
                         break;
                     tc::fence_after();
                     const uint32_t xa = xs_a + s * L.x_stage;
                     for (int ks = 0; ks < PA * 4; ++ks) {
-                        const uint64_t ad = tc::mdesc(xa + (ks >> 2) * 16384 + (ks & 3) * 32, 16, 1024);
-                        const uint64_t bd =
-                            tc::mdesc(b1_a + (ks >> 2) * (N1 * 128) + (ks & 3) * 32, 16, 1024);
-                        tc::mma(tmem + bb * N1, ad, bd, ID1, ks > 0 ? 1u : 0u);
+                        const uint64_t bd = tc::mdesc(xa + (ks >> 2) * 16384 + (ks & 3) * 32, 16, 1024);
+                        tc::mma_ta(tmem + kTcD1Col, tmem + kTcB1Col + ks * 8, bd, ID1, ks > 0 ? 1u : 0u);
                     }
-                    tc::commit(&d1_full[bb]);
+                    tc::commit(d1_full);
                 }
                 if (i >= 1) {
                     const int j = i - 1;
@@ -349,7 +389,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int ks = 0; ks < kTcRows / 16; ++ks) {
                             const uint64_t ad = tc::mdesc(xa + (2 * mb) * 16384 + ks * 16 * 128, 16384, 1024);
                             const uint64_t bd = tc::mdesc(rb_a + ks * 16 * 128, 16384, 1024);
-                            tc::mma(tmem + (2 + mb) * N1, ad, bd, ID2, (j > 0 || ks > 0) ? 1u : 0u);
+                            tc::mma(tmem + kTcD2Col + mb * 128, ad, bd, ID2, (j > 0 || ks > 0) ? 1u : 0u);
                         }
                     }
                     tc::commit(&x_empty[sj]);
@@ -364,119 +404,129 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc::commit(d2_done);
         }
     } else {
-        // ---- epilogue: one row per thread, KH vectors per warp --------------------------
+        // ---- epilogue ---------------------------------------------------------------------
+        constexpr int CW = kTcEpiCols;
+        constexpr int RT = kTcEpiRows;
         const int q = warp & 3;                 // tensor-memory lane quarter
-        const int hh = (warp - 2) >> 2;         // which half of the vectors
-        const int row = q * 32 + lane;
-        float facc[KH];
+        const int hh = (warp - 2) >> 2;         // tile rows CW*hh .. CW*hh + CW - 1
+        const int n = q * 32 + lane;            // D1 lane
+        const int k = n >> 1;                   // vector
+        const int part = n & 1;                 // 0: beta_hi lane, 1: beta_lo lane
+        const bool active = k < p.kk;
+        const int tb = CW * hh + RT * part;     // this thread's RT rows
+        float facc = 0.0f;
+        uint32_t yw[RT / 4], yn[RT / 4];
+        auto load_y = [&](int i, uint32_t *dst) {
 #pragma unroll
-        for (int k = 0; k < KH; ++k)
-            facc[k] = 0.0f;
-        auto load_y = [&](int i) -> float {
+            for (int w = 0; w < RT / 4; ++w)
+                dst[w] = 0u;
             if (i >= nt)
-                return 0.0f;
-            const int64_t r = (int64_t)(b + (int64_t)i * grid) * kTcRows + row;
-            return r < p.N ? (float)__ldg(p.y + r) : 0.0f;
+                return;
+            const int64_t r0 = (int64_t)(b + (int64_t)i * grid) * kTcRows + tb;
+            if (p.y_al4 && r0 + RT <= p.N) {
+                const uint32_t *yp = reinterpret_cast<const uint32_t *>(p.y + r0);
+#pragma unroll
+                for (int w = 0; w < RT / 4; ++w)
+                    dst[w] = __ldg(yp + w);
+            } else {
+                for (int j = 0; j < RT; ++j)
+                    if (r0 + j < p.N)
+                        dst[j >> 2] |= (uint32_t)__ldg(p.y + r0 + j) << (8 * (j & 3));
+            }
         };
-        float ycur = load_y(0);
+        load_y(0, yw);
         bool ok = true;
         for (int i = 0; i < nt; ++i) {
-            const int bb = i & 1;
-            const float ynext = load_y(i + 1);
-            if (!ptx::mbar_wait_bounded(&d1_full[bb], (unsigned)(i >> 1) & 1u, kSpinLimit)) {
+            load_y(i + 1, yn);
+            if (!ptx::mbar_wait_bounded(d1_full, (unsigned)i & 1u, kSpinLimit)) {
                 ok = false;
                 break;
             }
             tc::fence_after();
-            float dh[KH], dl[KH];
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + bb * N1 + hh * KH;
-            tc::tmem_ld<KH>(ta, dh);
-            tc::tmem_ld<KH>(ta + KB, dl);
+            float v[CW];
+            tc::tmem_ld<CW>(tmem + ((uint32_t)(q * 32) << 16) + kTcD1Col + CW * hh, v);
             tc::tmem_wait_ld();
             tc::fence_before();
             __syncwarp();
             if (lane == 0)
-                ptx::mbar_arrive(&d1_empty[bb]);
-            const bool valid = (int64_t)(b + (int64_t)i * grid) * kTcRows + row < p.N;
-            uint32_t rh[KH / 2], rl[KH / 2];
+                ptx::mbar_arrive(d1_empty);
+            const int64_t rbase = (int64_t)(b + (int64_t)i * grid) * kTcRows + tb;
+            const int64_t left = p.N - rbase;
+            const int nvalid = !active ? 0 : (left >= RT ? RT : (left > 0 ? (int)left : 0));
+            uint32_t w[RT];
 #pragma unroll
-            for (int k = 0; k < KH; k += 2) {
-                float ell0, r0, ell1, r1;
-                tc::tr_fast(dh[k] + dl[k], ycur, ell0, r0);
-                tc::tr_fast(dh[k + 1] + dl[k + 1], ycur, ell1, r1);
-                if (valid) {
-                    facc[k] += ell0;
-                    facc[k + 1] += ell1;
-                } else {
-                    r0 = 0.0f;
-                    r1 = 0.0f;
-                }
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0, r1);
-                const float2 hf = __bfloat1622float2(h2);
-                rh[k / 2] = *reinterpret_cast<const uint32_t *>(&h2);
-                rl[k / 2] = tc::pack_bf16(r0 - hf.x, r1 - hf.y);
+            for (int j = 0; j < RT; ++j) {
+                const float mine = part ? v[RT + j] : v[j];
+                const float send = part ? v[j] : v[RT + j];
+                const float eta = mine + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
+                const float yv = (float)((yw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                float ell, r;
+                tc::tr_fast(eta, yv, ell, r);
+                const bool in = j < nvalid;
+                facc += in ? ell : 0.0f;
+                r = in ? r : 0.0f;
+                const __nv_bfloat16 rh = __float2bfloat16_rn(r);
+                const float rhf = __bfloat162float(rh);
+                w[j] = tc::pack_bf16(rhf, r - rhf);
             }
             if (i >= 1 && !ptx::mbar_wait_bounded(r_empty, (unsigned)(i - 1) & 1u, kSpinLimit)) {
                 ok = false;
                 break;
             }
-            // R tile row `row`: columns n = hh*KH + k (hi) and KB + hh*KH + k (lo)
+            // R tile rows tb..tb+RT-1 (tb is a multiple of 8), columns 2k (hi)
+            // and 2k+1 (lo): the 128B swizzle permutes 16-byte chunks by row & 7
+            uint8_t *rrow = rb + (k >> 5) * 16384 + tb * 128 + (((2 * k) & 7) << 1);
+            const uint32_t chunk = (uint32_t)((2 * k) & 63) >> 3;
 #pragma unroll
-            for (int c = 0; c < KH / 8; ++c) {
-                const int nh = hh * KH + c * 8;
-                const int nl = KB + hh * KH + c * 8;
-                uint4 vh = make_uint4(rh[c * 4], rh[c * 4 + 1], rh[c * 4 + 2], rh[c * 4 + 3]);
-                uint4 vl = make_uint4(rl[c * 4], rl[c * 4 + 1], rl[c * 4 + 2], rl[c * 4 + 3]);
-                *reinterpret_cast<uint4 *>(rb + (nh >> 6) * 16384 + tc::sw128(row, nh & 63)) = vh;
-                *reinterpret_cast<uint4 *>(rb + (nl >> 6) * 16384 + tc::sw128(row, nl & 63)) = vl;
-            }
+            for (int j = 0; j < RT; ++j)
+                *reinterpret_cast<uint32_t *>(rrow + j * 128 + ((chunk ^ (uint32_t)(j & 7)) << 4)) = w[j];
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0)
                 ptx::mbar_arrive(r_full);
-            ycur = ynext;
+#pragma unroll
+            for (int t = 0; t < RT / 4; ++t)
+                yw[t] = yn[t];
         }
         if (!ok) {
             atomicOr(p.status, kDevTimeout);
             s_abort = 1;
         }
-        // g partial: D2 blocks, lane = column p of X, KH vectors per warp
         const int PP = MB * 128;
-        bool have = nt > 0 && ok && ptx::mbar_wait_bounded(d2_done, 0u, kSpinLimit);
+        const bool have = nt > 0 && ok && ptx::mbar_wait_bounded(d2_done, 0u, kSpinLimit);
         if (nt > 0 && !have) {
             atomicOr(p.status, kDevTimeout);
             s_abort = 1;
         }
         tc::fence_after();
-        // f partial of this CTA: rows of the warp, then the four lane quarters in
-        // order (the buffer lies in the R tile, idle now that every MMA is done)
-        asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
-#pragma unroll
-        for (int k = 0; k < KH; ++k) {
-            const double v = tc::warp_sum((double)facc[k]);
-            if (lane == 0)
-                sf[q * KB + hh * KH + k] = v;
-        }
+        // g partial: D2 block mb, lane = column p of X; this warp's CW/2 vectors
         for (int mb = 0; mb < MB; ++mb) {
-            float gh[KH], gl[KH];
+            float gv[CW];
             if (have) {
-                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (2 + mb) * N1 + hh * KH;
-                tc::tmem_ld<KH>(ta, gh);
-                tc::tmem_ld<KH>(ta + KB, gl);
+                tc::tmem_ld<CW>(tmem + ((uint32_t)(q * 32) << 16) + kTcD2Col + mb * 128 + CW * hh, gv);
                 tc::tmem_wait_ld();
             }
             const int pcol = mb * 128 + q * 32 + lane;
 #pragma unroll
-            for (int k = 0; k < KH; ++k) {
-                const float g = have ? gh[k] + gl[k] : 0.0f;
-                p.part_g[((size_t)b * KB + hh * KH + k) * PP + pcol] = g;
+            for (int kk2 = 0; kk2 < CW / 2; ++kk2) {
+                const int kv = (CW / 2) * hh + kk2;
+                if (kv < p.kk)
+                    p.part_g[((size_t)b * 64 + kv) * PP + pcol] =
+                        have ? gv[2 * kk2] + gv[2 * kk2 + 1] : 0.0f;
             }
         }
+        // f partial: the two lanes of a vector, then the row groups in order
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
+        const double fv = (double)facc + __shfl_xor_sync(0xFFFFFFFFu, (double)facc, 1);
+        if (part == 0)
+            sf[hh * 64 + k] = fv;
         asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
         const int et = tid - 64;
-        if (et < KB) {
-            const double v = sf[et] + sf[KB + et] + sf[2 * KB + et] + sf[3 * KB + et];
-            p.part_f[(size_t)b * KB + et] = s_abort ? __longlong_as_double(0x7FF8000000000000LL) : v;
+        if (et < p.kk) {
+            double tot = 0.0;
+            for (int g2 = 0; g2 < kTcEpiGroups; ++g2)
+                tot += sf[g2 * 64 + et];
+            p.part_f[(size_t)b * 64 + et] = s_abort ? __longlong_as_double(0x7FF8000000000000LL) : tot;
         }
     }
     tc::fence_before();
@@ -489,42 +539,56 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // Fixed-order combine of the per-CTA partials, plus the Gaussian prior.
-// Blocks [0, ng) produce g: one thread per (vector, column), loads batched so
-// that 16 are in flight before they are added in CTA order. The remaining
-// blocks produce f: one warp per vector, lanes over CTAs and over columns of
-// beta, finished by an exact butterfly.
-__global__ void tc_reduce_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g,
-                                 int parts, int KB, int PP, int P, int kk, int ng,
-                                 const float *__restrict__ beta, const float *__restrict__ x_scale,
-                                 double inv_s2, double prior_const, double *__restrict__ f_out,
-                                 float *__restrict__ g_out)
+// g: a block takes 32 consecutive columns of one vector; its 8 warps each add
+// a contiguous range of CTAs (all loads of a range in flight, coalesced over
+// the columns), then warp 0 adds the 8 range sums in order. f: one warp per
+// vector, lanes over CTAs and over columns of beta, finished by a butterfly.
+constexpr int kTcRedWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTcRedWarps)
+    tc_reduce_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g, int parts,
+                     int KB, int PP, int P, int kk, int ng, const float *__restrict__ beta,
+                     const float *__restrict__ x_scale, double inv_s2, double prior_const,
+                     double *__restrict__ f_out, float *__restrict__ g_out)
 {
     ptx::grid_dep_wait();
-    if ((int)blockIdx.x < ng) {
-        const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-        if (idx >= kk * P)
-            return;
-        const int k = idx / P;
-        const int jj = idx - k * P;
-        const float *src = part_g + (size_t)k * PP + jj;
-        const size_t stride = (size_t)KB * PP;
-        double v = 0.0;
-        for (int c0 = 0; c0 < parts; c0 += 16) {
-            float buf[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-                buf[u] = (c0 + u < parts) ? __ldg(src + (size_t)(c0 + u) * stride) : 0.0f;
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-                v += (double)buf[u];
-        }
-        const double sc = x_scale ? (double)x_scale[jj] : 1.0;
-        g_out[(size_t)k * P + jj] = (float)(sc * v - (double)beta[(size_t)k * P + jj] * inv_s2);
-        return;
-    }
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int k = ((int)blockIdx.x - ng) * (blockDim.x >> 5) + warp;
+    if ((int)blockIdx.x < ng) {
+        __shared__ double part_sum[kTcRedWarps][32];
+        const int cpk = (P + 31) / 32;                 // column blocks per vector
+        const int k = blockIdx.x / cpk;
+        const int jj = (blockIdx.x - k * cpk) * 32 + lane;
+        const int per = (parts + kTcRedWarps - 1) / kTcRedWarps;
+        const int c0 = warp * per;
+        const int c1 = (c0 + per) < parts ? (c0 + per) : parts;
+        double v = 0.0;
+        if (jj < P) {
+            const float *src = part_g + (size_t)k * PP + jj;
+            const size_t stride = (size_t)KB * PP;
+            for (int cb = c0; cb < c1; cb += 32) {
+                float buf[32];
+#pragma unroll
+                for (int u = 0; u < 32; ++u)
+                    buf[u] = (cb + u < c1) ? __ldg(src + (size_t)(cb + u) * stride) : 0.0f;
+#pragma unroll
+                for (int u = 0; u < 32; ++u)
+                    v += (double)buf[u];
+            }
+        }
+        part_sum[warp][lane] = v;
+        __syncthreads();
+        if (warp == 0 && jj < P) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < kTcRedWarps; ++w)
+                t += part_sum[w][lane];
+            const double sc = x_scale ? (double)x_scale[jj] : 1.0;
+            g_out[(size_t)k * P + jj] = (float)(sc * t - (double)beta[(size_t)k * P + jj] * inv_s2);
+        }
+        return;
+    }
+    const int k = ((int)blockIdx.x - ng) * kTcRedWarps + warp;
     if (k >= kk)
         return;
     double v = 0.0;
@@ -552,10 +616,10 @@ bool tc_supported(const glm_ctx *h)
            std::getenv("GLM_NO_TC") == nullptr;
 }
 
-static int tc_stages(int PA, int KB)
+static int tc_stages(int PA)
 {
     int st = kTcMaxStages;
-    while (st >= 2 && tc_layout(PA, KB, st).total > 232448)
+    while (st >= 2 && tc_layout(PA, st).total > 232448)
         --st;
     return st;
 }
@@ -610,25 +674,25 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(h->tc_map);
     for (int k0 = 0; k0 < K; k0 += kTcMaxKB) {
         const int kk = (K - k0) < kTcMaxKB ? (K - k0) : kTcMaxKB;
-        const int KB = kk <= 16 ? 16 : (kk <= 32 ? 32 : 64);
+        const int KB = kTcMaxKB;
         TcParams prm;
         std::memset(&prm, 0, sizeof(prm));
         prm.y = y;
+        prm.y_al4 = (reinterpret_cast<uintptr_t>(y) & 3u) == 0 ? 1 : 0;
         prm.beta = beta + (size_t)k0 * P;
         prm.N = h->d.n_rows;
         prm.P = P;
         prm.kk = kk;
         prm.PA = PA;
         prm.MB = MB;
-        prm.stages = tc_stages(PA, KB);
+        prm.stages = tc_stages(PA);
         if (prm.stages < 2)
             return GLM_ERR_UNSUPPORTED;
         prm.part_f = h->tc_part_f;
         prm.part_g = h->tc_part_g;
         prm.status = h->status;
-        auto fn = KB == 16 ? &tc_logpost_grad_kernel<16>
-                           : (KB == 32 ? &tc_logpost_grad_kernel<32> : &tc_logpost_grad_kernel<64>);
-        const TcLayout L = tc_layout(PA, KB, prm.stages);
+        auto fn = &tc_logpost_grad_kernel;
+        const TcLayout L = tc_layout(PA, prm.stages);
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) !=
             cudaSuccess)
             return GLM_ERR_CUDA;
@@ -644,11 +708,11 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         cfg.numAttrs = 1;
         if (cudaLaunchKernelEx(&cfg, fn, *map, prm) != cudaSuccess)
             return GLM_ERR_CUDA;
-        const int ng = (kk * P + 255) / 256;
-        const int nf = (kk + 7) / 8;
+        const int ng = kk * ((P + 31) / 32);
+        const int nf = (kk + kTcRedWarps - 1) / kTcRedWarps;
         cudaLaunchConfig_t rc = {};
         rc.gridDim = dim3((unsigned)(ng + nf));
-        rc.blockDim = dim3(256);
+        rc.blockDim = dim3(32 * kTcRedWarps);
         rc.stream = s;
         rc.attrs = attr;
         rc.numAttrs = 1;
