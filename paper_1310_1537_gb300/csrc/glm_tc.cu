@@ -454,20 +454,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int64_t left = p.N - rbase;
             const int nvalid = !active ? 0 : (left >= RT ? RT : (left > 0 ? (int)left : 0));
             uint32_t w[RT];
+            // hi/lo lanes of a vector each keep their own RT rows: swap the
+            // other half with the partner lane and add
+            float mine[RT];
 #pragma unroll
             for (int j = 0; j < RT; ++j) {
-                const float mine = part ? v[RT + j] : v[j];
                 const float send = part ? v[j] : v[RT + j];
-                const float eta = mine + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
-                const float yv = (float)((yw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
-                float ell, r;
-                tc::tr_fast(eta, yv, ell, r);
-                const bool in = j < nvalid;
-                facc += in ? ell : 0.0f;
-                r = in ? r : 0.0f;
-                const __nv_bfloat16 rh = __float2bfloat16_rn(r);
-                const float rhf = __bfloat162float(rh);
-                w[j] = tc::pack_bf16(rhf, r - rhf);
+                mine[j] = (part ? v[RT + j] : v[j]) + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
+            }
+            if (nvalid == RT) {
+#pragma unroll
+                for (int j = 0; j < RT; ++j) {
+                    const float yv = (float)((yw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                    float ell, r;
+                    tc::tr_fast(mine[j], yv, ell, r);
+                    facc += ell;
+                    const __nv_bfloat16 rh = __float2bfloat16_rn(r);
+                    const float rhf = __bfloat162float(rh);
+                    w[j] = tc::pack_bf16(rhf, r - rhf);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < RT; ++j) {
+                    const float yv = (float)((yw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                    float ell, r;
+                    tc::tr_fast(mine[j], yv, ell, r);
+                    const bool in = j < nvalid;
+                    facc += in ? ell : 0.0f;
+                    r = in ? r : 0.0f;
+                    const __nv_bfloat16 rh = __float2bfloat16_rn(r);
+                    const float rhf = __bfloat162float(rh);
+                    w[j] = tc::pack_bf16(rhf, r - rhf);
+                }
             }
             if (i >= 1 && !ptx::mbar_wait_bounded(r_empty, (unsigned)(i - 1) & 1u, kSpinLimit)) {
                 ok = false;
