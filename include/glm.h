@@ -63,7 +63,8 @@ typedef enum {
     GLM_ERR_OOM = 3,           /* workspace allocation failed                 */
     GLM_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed        */
     GLM_ERR_TIMEOUT = 5,       /* a device-side bounded wait expired          */
-    GLM_ERR_NO_DEVICE = 6      /* no usable sm_103 device                     */
+    GLM_ERR_NO_DEVICE = 6,     /* no usable sm_103 device                     */
+    GLM_PENDING = 7            /* glm_server_poll: result not ready yet       */
 } glm_status_t;
 
 typedef enum {
@@ -278,6 +279,115 @@ GLM_API glm_status_t glm_logpost_grad_noalloc(const void *X, const float *x_scal
                                               int32_t ld, int32_t xtype, double prior_sigma,
                                               const float *beta, int32_t K, double *f_out,
                                               float *g_out, glm_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Serving loop with continuous batching.
+ *
+ * The paper evaluates one posterior at a time; it has no serving layer. This
+ * is a deployment layer over glm_logpost_grad for many clients that ask for
+ * f and g of their own coefficient vectors against datasets held resident on
+ * one GPU.
+ *
+ * A server owns a scheduler thread, a pool of `streams` CUDA streams, pinned
+ * host staging per stream and one device arena of `hbm_budget_bytes` for the
+ * batches in flight (0 = one eighth of the device's free memory, capped at
+ * one half). Requests are queued in arrival order. The scheduler takes the
+ * oldest waiting request, merges every later waiting request for the same
+ * dataset while the merged batch holds at most max_batch_k vectors, and runs
+ * the batch on a free stream as soon as the arena has room for its
+ * coefficient, f and g buffers (admission by free device memory; a batch
+ * that does not fit waits for a completion). Batches for different datasets
+ * run concurrently on different streams.
+ *
+ * Each vector's result is the one glm_logpost_grad gives for it in a batch
+ * of that batch's size: batches of 16 or more BF16 vectors take the
+ * tensor-core path, smaller ones the CUDA-core path, so a result alone and
+ * inside a mix agree to the evaluation tolerance.
+ * ---------------------------------------------------------------------- */
+typedef struct glm_server *glm_server_t;
+
+typedef struct {
+    int32_t device;            /* CUDA device                                  */
+    int32_t streams;           /* stream slots, 1..16                          */
+    int32_t max_batch_k;       /* largest merged batch in vectors, 1..1024     */
+    int32_t max_pending;       /* queue limit; submit past it returns OOM      */
+    int64_t hbm_budget_bytes;  /* arena for batches in flight (0 = default)    */
+} glm_server_desc_t;
+
+typedef struct {
+    int64_t submit_ns;         /* steady-clock times of the request's life     */
+    int64_t start_ns;          /* batch launched                               */
+    int64_t done_ns;           /* results copied back to the host              */
+    int32_t batch_k;           /* vectors in the batch that carried it         */
+    int32_t batch_requests;    /* requests merged into that batch              */
+    int32_t k;                 /* this request's vectors                       */
+    int32_t status;            /* glm_status_t of the request                  */
+} glm_request_info_t;
+
+typedef struct {
+    int64_t requests_done;
+    int64_t requests_failed;
+    int64_t requests_waiting;
+    int64_t batches;
+    int64_t vectors_done;
+    int64_t hbm_budget_bytes;
+    int64_t hbm_in_flight_bytes;
+    int32_t max_concurrent_batches;
+    int32_t last_cuda_error;   /* cudaError_t of the last failed step (0: none) */
+    int32_t last_error_site;   /* glm_server_error_site_t of that step          */
+} glm_server_stats_t;
+
+/* Where a failed batch failed (glm_server_stats_t.last_error_site). */
+typedef enum {
+    GLM_SERVER_SITE_NONE = 0,
+    GLM_SERVER_SITE_COPY_IN = 1,      /* coefficients host -> device         */
+    GLM_SERVER_SITE_EVALUATE = 2,     /* glm_logpost_grad refused or failed  */
+    GLM_SERVER_SITE_COPY_OUT = 3,     /* f, g or status device -> host       */
+    GLM_SERVER_SITE_COMPLETION = 4,   /* completion callback not enqueued    */
+    GLM_SERVER_SITE_DEVICE_WAIT = 5   /* a bounded device wait expired       */
+} glm_server_error_site_t;
+
+/* Create a server on desc->device. Returns GLM_ERR_NO_DEVICE without a GPU,
+ * GLM_ERR_INVALID_ARG on a bad descriptor, GLM_ERR_OOM if the arena cannot
+ * be allocated. */
+GLM_API glm_status_t glm_server_create(const glm_server_desc_t *desc, glm_server_t *out);
+
+/* Register a device-resident dataset (same layout and storage types as the
+ * handle API: X row-major n_rows x ld, y n_rows bytes, x_scale for FP8). The
+ * caller keeps X, x_scale and y alive and unchanged until glm_server_destroy.
+ * Creates one evaluation handle per stream slot. Returns the dataset's id. */
+GLM_API glm_status_t glm_server_add_dataset(glm_server_t s, const void *X, const float *x_scale,
+                                            const uint8_t *y, int64_t n_rows, int32_t p,
+                                            int32_t ld, int32_t xtype, double prior_sigma,
+                                            int32_t *dataset_id);
+
+/* Queue a request: K (1..max_batch_k) FP32 vectors beta_host[K x P] in HOST
+ * memory, copied before the call returns. Returns a request id, or
+ * GLM_ERR_OOM when max_pending requests are already waiting. Thread-safe. */
+GLM_API glm_status_t glm_server_submit(glm_server_t s, int32_t dataset_id, const float *beta_host,
+                                       int32_t K, uint64_t *request_id);
+
+/* Non-blocking: GLM_PENDING while the request runs; when it has finished,
+ * copies f (K FP64) and g (K x P FP32) into the HOST buffers given (either
+ * may be NULL), fills *info if not NULL, forgets the request and returns its
+ * status: GLM_OK, the error glm_logpost_grad returned for its batch,
+ * GLM_ERR_CUDA when a copy or launch of the batch failed, or GLM_ERR_TIMEOUT
+ * when a bounded device wait of the batch expired (results not valid). An
+ * unknown id returns GLM_ERR_INVALID_ARG. */
+GLM_API glm_status_t glm_server_poll(glm_server_t s, uint64_t request_id, double *f_host,
+                                     float *g_host, glm_request_info_t *info);
+
+/* Blocking form of glm_server_poll, waiting up to timeout_ms milliseconds
+ * (GLM_ERR_TIMEOUT if the request has not finished by then; it stays queued). */
+GLM_API glm_status_t glm_server_wait(glm_server_t s, uint64_t request_id, double *f_host,
+                                     float *g_host, glm_request_info_t *info, int32_t timeout_ms);
+
+/* Counters since creation. */
+GLM_API glm_status_t glm_server_stats(glm_server_t s, glm_server_stats_t *stats);
+
+/* Stop the scheduler, drain the streams and free everything the server owns
+ * (not the datasets' memory). Requests still waiting are dropped. */
+GLM_API glm_status_t glm_server_destroy(glm_server_t s);
 
 #ifdef __cplusplus
 }

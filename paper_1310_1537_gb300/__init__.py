@@ -22,6 +22,7 @@ GLM_ERR_OOM = 3
 GLM_ERR_CUDA = 4
 GLM_ERR_TIMEOUT = 5
 GLM_ERR_NO_DEVICE = 6
+GLM_PENDING = 7
 
 GLM_X_F32 = 0
 GLM_X_BF16 = 1
@@ -36,7 +37,8 @@ EXPORTS = (
     "glm_create", "glm_destroy", "glm_status_str", "glm_get_info", "glm_logpost_grad",
     "glm_logpost_grad_host", "glm_logpost_grad_grouped", "glm_rwm_run", "glm_quantize",
     "glm_sync", "glm_selftest_wait_timeout", "glm_logpost_grad_noalloc",
-    "glm_autotune_grouped",
+    "glm_autotune_grouped", "glm_server_create", "glm_server_add_dataset", "glm_server_submit",
+    "glm_server_poll", "glm_server_wait", "glm_server_stats", "glm_server_destroy",
 )
 
 
@@ -56,6 +58,25 @@ class glm_info_t(C.Structure):
     _fields_ = [("sm_count", C.c_int32), ("grid", C.c_int32), ("tile_rows", C.c_int32),
                 ("stages", C.c_int32), ("smem_bytes", C.c_int32), ("tc_enabled", C.c_int32),
                 ("tc_min_k", C.c_int32), ("workspace_bytes", C.c_int64)]
+
+
+class glm_server_desc_t(C.Structure):
+    _fields_ = [("device", C.c_int32), ("streams", C.c_int32), ("max_batch_k", C.c_int32),
+                ("max_pending", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+
+
+class glm_request_info_t(C.Structure):
+    _fields_ = [("submit_ns", C.c_int64), ("start_ns", C.c_int64), ("done_ns", C.c_int64),
+                ("batch_k", C.c_int32), ("batch_requests", C.c_int32), ("k", C.c_int32),
+                ("status", C.c_int32)]
+
+
+class glm_server_stats_t(C.Structure):
+    _fields_ = [("requests_done", C.c_int64), ("requests_failed", C.c_int64),
+                ("requests_waiting", C.c_int64), ("batches", C.c_int64),
+                ("vectors_done", C.c_int64), ("hbm_budget_bytes", C.c_int64),
+                ("hbm_in_flight_bytes", C.c_int64), ("max_concurrent_batches", C.c_int32),
+                ("last_cuda_error", C.c_int32), ("last_error_site", C.c_int32)]
 
 
 _lib = None
@@ -94,6 +115,15 @@ def load(build_if_missing: bool = True):
                                           C.c_double, vp, C.c_int32, vp, vp, vp], st),
             "glm_autotune_grouped": ([vp, vp, vp, vp, vp, C.c_int32, vp, vp, C.c_double, vp, vp,
                                       C.c_int32, vp], st),
+            "glm_server_create": ([C.POINTER(glm_server_desc_t), C.POINTER(vp)], st),
+            "glm_server_add_dataset": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32,
+                                        C.c_int32, C.c_double, C.POINTER(C.c_int32)], st),
+            "glm_server_submit": ([vp, C.c_int32, vp, C.c_int32, C.POINTER(C.c_uint64)], st),
+            "glm_server_poll": ([vp, C.c_uint64, vp, vp, C.POINTER(glm_request_info_t)], st),
+            "glm_server_wait": ([vp, C.c_uint64, vp, vp, C.POINTER(glm_request_info_t),
+                                 C.c_int32], st),
+            "glm_server_stats": ([vp, C.POINTER(glm_server_stats_t)], st),
+            "glm_server_destroy": ([vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -212,3 +242,62 @@ def glm_logpost_grad_noalloc(X, x_scale, y, n_rows, p, ld, xtype, prior_sigma, b
                                            int(ld), int(xtype), float(prior_sigma), _ptr(beta),
                                            int(K), _ptr(f_out), _ptr(g_out), _stream(stream)),
            "glm_logpost_grad_noalloc")
+
+
+def _info_dict(info) -> dict:
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def glm_server_create(device: int = 0, streams: int = 4, max_batch_k: int = 64,
+                      max_pending: int = 65536, hbm_budget_bytes: int = 0):
+    """Create a serving loop (scheduler thread + stream pool); returns the server."""
+    d = glm_server_desc_t(int(device), int(streams), int(max_batch_k), int(max_pending),
+                          int(hbm_budget_bytes))
+    s = C.c_void_p()
+    _check(load().glm_server_create(C.byref(d), C.byref(s)), "glm_server_create")
+    return s.value
+
+
+def glm_server_add_dataset(s, X, x_scale, y, n_rows, p, ld, xtype=GLM_X_F32,
+                           prior_sigma=10.0) -> int:
+    ds = C.c_int32()
+    _check(load().glm_server_add_dataset(s, _ptr(X), _ptr(x_scale), _ptr(y), int(n_rows), int(p),
+                                         int(ld), int(xtype), float(prior_sigma), C.byref(ds)),
+           "glm_server_add_dataset")
+    return ds.value
+
+
+def glm_server_submit(s, dataset_id, beta_host, K) -> int:
+    """Queue K host FP32 vectors (contiguous K x P); returns the request id."""
+    rid = C.c_uint64()
+    _check(load().glm_server_submit(s, int(dataset_id), _ptr(beta_host), int(K), C.byref(rid)),
+           "glm_server_submit")
+    return rid.value
+
+
+def glm_server_poll(s, request_id, f_host=None, g_host=None):
+    """Returns None while pending, else the request's info dict (raises on failure)."""
+    info = glm_request_info_t()
+    st = load().glm_server_poll(s, C.c_uint64(request_id), _ptr(f_host), _ptr(g_host),
+                                C.byref(info))
+    if st == GLM_PENDING:
+        return None
+    _check(st, "glm_server_poll")
+    return _info_dict(info)
+
+
+def glm_server_wait(s, request_id, f_host=None, g_host=None, timeout_ms=60000) -> dict:
+    info = glm_request_info_t()
+    _check(load().glm_server_wait(s, C.c_uint64(request_id), _ptr(f_host), _ptr(g_host),
+                                  C.byref(info), int(timeout_ms)), "glm_server_wait")
+    return _info_dict(info)
+
+
+def glm_server_stats(s) -> dict:
+    st = glm_server_stats_t()
+    _check(load().glm_server_stats(s, C.byref(st)), "glm_server_stats")
+    return _info_dict(st)
+
+
+def glm_server_destroy(s) -> None:
+    _check(load().glm_server_destroy(s), "glm_server_destroy")

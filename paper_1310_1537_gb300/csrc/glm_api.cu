@@ -4,7 +4,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <mutex>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "glm_internal.cuh"
 
@@ -45,8 +48,9 @@ glm_status_t launch_fused(glm_ctx *h, const FusedParams &p, int kc, cudaStream_t
     }
 }
 
-// Shared-memory budget per CTA on sm_103 (227 KB opt-in).
-constexpr int kSmemOptin = 232448;
+// Dynamic shared-memory budget per CTA: the 227 KB opt-in limit less room
+// for the kernel's static shared arrays.
+constexpr int kSmemOptin = kSmemDynamicBudget;
 
 static int fused_smem_total(const glm_ctx *h, int tile_rows, int stages, int kc)
 {
@@ -226,6 +230,29 @@ static glm_status_t fused_eval(glm_ctx *h, const void *X, const float *x_scale, 
     return GLM_OK;
 }
 
+cudaError_t allow_max_dynamic_smem(const void *fn)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;   // (kernel, device)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &d : done)
+        if (d.first == fn && d.second == dev)
+            return cudaSuccess;
+    cudaFuncAttributes a;
+    e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemOptinBytes - (int)a.sharedSizeBytes);
+    if (e == cudaSuccess)
+        done.push_back({fn, dev});
+    return e;
+}
+
 }  // namespace glm
 
 using namespace glm;
@@ -242,6 +269,7 @@ const char *glm_status_str(glm_status_t s)
     case GLM_ERR_CUDA: return "CUDA error";
     case GLM_ERR_TIMEOUT: return "device wait timed out";
     case GLM_ERR_NO_DEVICE: return "no usable CUDA device";
+    case GLM_PENDING: return "pending";
     default: return "unknown status";
     }
 }

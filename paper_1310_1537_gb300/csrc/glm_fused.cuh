@@ -547,8 +547,7 @@ glm_status_t launch_fused_t(glm_ctx *h, const FusedParams &prm, int kc, cudaStre
 #undef GLM_PICK
     if (!fn)
         return GLM_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) !=
-        cudaSuccess)
+    if (allow_max_dynamic_smem(reinterpret_cast<const void *>(fn)) != cudaSuccess)
         return GLM_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)h->grid);

@@ -822,7 +822,7 @@ glm_status_t grouped_configure(glm_ctx *h)
     int per_sm = env_int("GLM_GROUPED_CTAS_PER_SM", 1);
     if (per_sm < 1 || per_sm > 4)
         per_sm = 1;
-    const int budget = 232448 / per_sm - (per_sm > 1 ? 1024 : 0);
+    const int budget = kSmemOptinBytes / per_sm - (per_sm > 1 ? 1024 : 0);
     // 32-row units per TMA slot (narrow rows only): bigger slots keep more
     // bytes in flight per warp
     int units = narrow ? (kGroupedRows * row_bytes <= 4096 ? 2 : 1) : 1;
@@ -920,7 +920,7 @@ glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, con
         break;
     default: return GLM_ERR_UNSUPPORTED;
     }
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (allow_max_dynamic_smem(reinterpret_cast<const void *>(fn)) != cudaSuccess)
         return GLM_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)h->gr_grid);
@@ -968,7 +968,7 @@ glm_status_t autotune_grouped(glm_ctx *h, const void *X, const float *x_scale, c
                 continue;
             for (int units = 1; units <= (nar ? 4 : 1) && st == GLM_OK; units <<= 1) {
                 for (int per_sm = 1; per_sm <= 2 && st == GLM_OK; ++per_sm) {
-                    const int budget = 232448 / per_sm - (per_sm > 1 ? 1024 : 0);
+                    const int budget = kSmemOptinBytes / per_sm - (per_sm > 1 ? 1024 : 0);
                     for (int stages = 2; stages <= 4 && st == GLM_OK; ++stages) {
                         if (grouped_smem(row_bytes, warps, stages, pcue, nar, units) > budget)
                             continue;

@@ -20,6 +20,13 @@ constexpr unsigned kDevTimeout = 1u;
 // is far above any legitimate wait yet ends in well under a minute.
 constexpr unsigned kSpinLimit = 1u << 24;
 
+// Opt-in shared memory per block on sm_103 (227 KB), static and dynamic
+// together, and the part of it the configurators leave for the kernels'
+// static __shared__ arrays (at most 768 bytes in any kernel here).
+constexpr int kSmemOptinBytes = 232448;
+constexpr int kSmemStaticReserve = 1024;
+constexpr int kSmemDynamicBudget = kSmemOptinBytes - kSmemStaticReserve;
+
 constexpr int kFusedThreads = 256;
 constexpr int kMaxStages = 8;
 
@@ -136,6 +143,12 @@ glm_status_t fused_configure(glm_ctx *h);
 glm_status_t launch_quantize(glm_ctx *h, const float *X32, int ld32, void *Xq, float *x_scale,
                              cudaStream_t s);
 glm_status_t launch_wait_timeout(glm_ctx *h, int spin_limit, cudaStream_t s);
+// Raise a kernel's dynamic shared-memory cap to the most a block may use on
+// the current device (the 227 KB opt-in limit less the kernel's static shared
+// memory). The cap is the same on every call, so host threads that launch
+// the same kernel concurrently with different sizes cannot lower it between
+// another thread's set and launch. Done once per (kernel, device).
+cudaError_t allow_max_dynamic_smem(const void *fn);
 glm_status_t grouped_configure(glm_ctx *h);
 size_t tc_workspace_bytes(const glm_ctx *h);
 glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,

@@ -637,7 +637,7 @@ bool tc_supported(const glm_ctx *h)
 static int tc_stages(int PA)
 {
     int st = kTcMaxStages;
-    while (st >= 2 && tc_layout(PA, st).total > 232448)
+    while (st >= 2 && tc_layout(PA, st).total > kSmemDynamicBudget)
         --st;
     return st;
 }
@@ -711,8 +711,7 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         prm.status = h->status;
         auto fn = &tc_logpost_grad_kernel;
         const TcLayout L = tc_layout(PA, prm.stages);
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) !=
-            cudaSuccess)
+        if (allow_max_dynamic_smem(reinterpret_cast<const void *>(fn)) != cudaSuccess)
             return GLM_ERR_CUDA;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)h->sm_count);

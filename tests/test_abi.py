@@ -81,3 +81,32 @@ def test_create_without_device_reports_no_device():
         assert e.status == pkg.GLM_ERR_NO_DEVICE
     else:
         pytest.fail("glm_create succeeded without a device")
+
+
+def test_server_rejects_bad_descriptors_and_null_arguments():
+    import ctypes as C
+    lib = pkg.load()
+    s = C.c_void_p()
+    assert lib.glm_server_create(None, C.byref(s)) == pkg.GLM_ERR_INVALID_ARG
+    for b in [(0, 0, 8, 16, 0), (0, 17, 8, 16, 0), (0, 2, 0, 16, 0), (0, 2, 1025, 16, 0),
+              (0, 2, 8, 0, 0), (0, 2, 8, 16, -1), (-1, 2, 8, 16, 0)]:
+        d = pkg.glm_server_desc_t(*b)
+        assert lib.glm_server_create(C.byref(d), C.byref(s)) == pkg.GLM_ERR_INVALID_ARG, b
+        assert s.value is None
+    rid = C.c_uint64()
+    ds = C.c_int32()
+    assert lib.glm_server_submit(None, 0, None, 1, C.byref(rid)) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_server_add_dataset(None, None, None, None, 1, 1, 4, 0, 10.0,
+                                      C.byref(ds)) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_server_poll(None, 1, None, None, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_server_stats(None, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_server_destroy(None) == pkg.GLM_OK
+    assert pkg.glm_status_str(pkg.GLM_PENDING) == "pending"
+
+
+@pytest.mark.skipif(__import__("tests.conftest", fromlist=["gpu_available"]).gpu_available(),
+                    reason="checks the no-device path")
+def test_server_without_device_reports_no_device():
+    with pytest.raises(pkg.GLMError) as e:
+        pkg.glm_server_create(0, 2, 8, 16)
+    assert e.value.status == pkg.GLM_ERR_NO_DEVICE

@@ -182,3 +182,43 @@ def test_big_workload_full_size():
         f_o, g_o = _oracle(d.X, d.y, B[k], 100)
         ef, eg = assert_close(f, g, f_o, g_o, what="big workload")
         print(f"big: f rel {ef:.2e} g rel {eg:.2e}")
+
+
+@pytest.mark.parametrize("xtype", [glm.GLM_X_F32, glm.GLM_X_BF16, glm.GLM_X_FP8E4M3])
+def test_every_row_width_configures_and_launches(xtype):
+    """Row widths from 1 to 520 columns at the largest CUDA-core chunk
+    (8 vectors; 4 for FP8): the configurator's tile, stage and split choice
+    must fit the per-block shared-memory limit together with the kernel's
+    static shared arrays, and the results must match the oracle on the same
+    stored X (rounded by the oracle's own BF16 / E4M3 encoders)."""
+    t = torch()
+    es = glm.ELEM_BYTES[xtype]
+    k = 4 if xtype == glm.GLM_X_FP8E4M3 else 8
+    n = 300
+    for p in list(range(1, 80)) + list(range(80, 521, 9)):
+        d = synth.make_glm(n, p, 4000 + p, dtype=np.float32)
+        ld = synth.padded_ld(p, es)
+        Xs = synth.pad_columns(d.X, ld)
+        xs = None
+        if xtype == glm.GLM_X_F32:
+            Xstore, Xr = Xs, Xs.astype(np.float64)
+        elif xtype == glm.GLM_X_BF16:
+            Xstore = oracle.bf16_from_f32(Xs)
+            Xr = oracle.bf16_to_f64(Xstore)
+        else:
+            Xstore, sc = oracle.quantize_e4m3(d.X, p, ld)
+            Xr = oracle.dequantize_e4m3(Xstore, sc)
+            xs = sc
+        h = Handle(Xstore, d.y, p, xtype=xtype, k_max=k, x_scale=xs,
+                   flags=glm.GLM_FLAG_NO_TENSOR_CORES)
+        try:
+            rng = np.random.default_rng(p)
+            # a spread well away from the mode, so that g is not a near-zero
+            # difference of large sums (P = 1 is the intercept alone)
+            B = (d.beta_star[None, :] + 0.5 * rng.standard_normal((k, p))).astype(np.float32)
+            f, g = h.eval(B)
+            f_o, g_o = oracle.logpost_grad(Xr, d.y, B.astype(np.float64), p=p)
+            assert_close(f, g, f_o, g_o, f_rtol=1e-4, g_rtol=1e-4,
+                         what=f"xtype={xtype} P={p} ld={ld}")
+        finally:
+            h.close()
