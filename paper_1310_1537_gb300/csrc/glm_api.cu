@@ -52,17 +52,17 @@ glm_status_t launch_fused(glm_ctx *h, const FusedParams &p, int kc, cudaStream_t
 // for the kernel's static shared arrays.
 constexpr int kSmemOptin = kSmemDynamicBudget;
 
-static int fused_smem_total(const glm_ctx *h, int tile_rows, int stages, int kc)
+static int fused_smem_total(const glm_ctx *h, int tile_rows, int stages, int kc, int srow)
 {
     const int es = h->elem_bytes;
     const int epc = 16 / es;
     const int pce = (h->d.ld / epc) * epc;
-    const int stage = tile_rows * h->d.ld * es;
+    const int stage = tile_rows * srow;
     const int red = kFusedThreads * kc * epc * 4;
     int tiles = stages * stage > red ? stages * stage : red;
     tiles = (tiles + 127) / 128 * 128;
     return tiles + (kc * pce * 4 + 15) / 16 * 16 + (tile_rows * kc * 4 + 15) / 16 * 16 +
-           kMaxStages * 8 + 64;
+           kMaxStages * 8 + 64 + 128;
 }
 
 // Choose the phase-1 split (threads per row), the rows per staged tile and the
@@ -76,11 +76,20 @@ glm_status_t fused_configure(glm_ctx *h)
         return GLM_ERR_UNSUPPORTED;
     h->kc_max = (epc <= 8) ? 8 : 4;
     const int row_bytes = h->d.ld * es;
+    const int pc = row_bytes / 16;
+    // Staged row stride for a split: one zero chunk wider when the chunk
+    // count is even and rows are read one thread per row (SPLIT <= 4), so
+    // that 8 consecutive rows start in distinct bank groups. The extra chunk
+    // comes from a 2-D tensor copy of 8-byte words whose box is wider than the
+    // row (box dimensions are at most 256 elements, so rows up to 2032 bytes).
+    const bool pad_ok = h->d.n_rows > 0 && pc % 2 == 0 && row_bytes + 16 <= 256 * 8 &&
+                        env_int("GLM_FUSED_NO_PAD", 0) == 0 && tensor_map_encoder() != nullptr;
+    auto srow_for = [&](int sp) { return (pad_ok && sp != 32) ? row_bytes + 16 : row_bytes; };
     // Fewest threads per row whose one-batch tile still fits two stages:
     // bigger tiles amortise the per-tile barriers and label loads.
     int split = 32;
     for (int cand = 1; cand <= 4; cand <<= 1) {
-        if (fused_smem_total(h, kFusedThreads / cand, 2, h->kc_max) <= kSmemOptin) {
+        if (fused_smem_total(h, kFusedThreads / cand, 2, h->kc_max, srow_for(cand)) <= kSmemOptin) {
             split = cand;
             break;
         }
@@ -93,10 +102,11 @@ glm_status_t fused_configure(glm_ctx *h)
         per_sm = 1;
     const int budget = kSmemOptin / per_sm - (per_sm > 1 ? 1024 : 0);
     int rb = kFusedThreads / split;
+    int srow = srow_for(split);
     int target = env_int("GLM_FUSED_STAGE_BYTES", 49152);
     // rows per tile: a multiple of the phase-1 batch, at most four batches
     auto pick_rows = [&](int rbv) {
-        int t = (target / row_bytes) / rbv * rbv;
+        int t = (target / srow) / rbv * rbv;
         if (t < rbv)
             t = rbv;
         if (t > 4 * rbv)
@@ -111,14 +121,15 @@ glm_status_t fused_configure(glm_ctx *h)
             T = 4 * rb;
     }
     int stages = kMaxStages;
-    while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max) > budget)
+    while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max, srow) > budget)
         --stages;
     if (stages < 2 && split != 32) {     // rows too wide: one warp per row, 8-row batches
         split = 32;
         rb = kFusedThreads / split;
+        srow = srow_for(split);
         T = pick_rows(rb);
         stages = kMaxStages;
-        while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max) > budget)
+        while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max, srow) > budget)
             --stages;
     }
     if (stages < 2)
@@ -129,7 +140,17 @@ glm_status_t fused_configure(glm_ctx *h)
     h->split = split;
     h->stages = stages;
     h->tile_rows = T;
-    h->smem_bytes = fused_smem_total(h, T, stages, h->kc_max);
+    h->srow = srow;
+    h->box_rows = 0;
+    if (srow != row_bytes) {
+        // rows per tensor copy: the largest power of two up to 256 dividing T
+        int br = 256;
+        while (br > 8 && T % br != 0)
+            br >>= 1;
+        h->box_rows = br;
+    }
+    h->fx_map_ptr = nullptr;
+    h->smem_bytes = fused_smem_total(h, T, stages, h->kc_max, srow);
     h->grid = h->sm_count * per_sm;
     h->use_pdl = env_int("GLM_NO_PDL", 0) ? 0 : 1;
     const int g = env_int("GLM_FUSED_GRID", 0);
@@ -191,6 +212,8 @@ static FusedParams base_params(const glm_ctx *h, const void *X, const float *x_s
     p.ld = h->d.ld;
     p.stages = h->stages;
     p.tile_rows = h->tile_rows;
+    p.srow = h->srow;
+    p.box_rows = h->box_rows;
     const double s2 = h->d.prior_sigma * h->d.prior_sigma;
     p.inv_s2 = 1.0 / s2;
     p.prior_const = 0.5 * (double)h->d.p * std::log(2.0 * M_PI * s2);
@@ -227,6 +250,48 @@ static glm_status_t fused_eval(glm_ctx *h, const void *X, const float *x_scale, 
             return st;
         k0 += kk;
     }
+    return GLM_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// X viewed as rows of 8-byte words: {word within the row, row}. The box is
+// two words (one chunk) wider than a row; those words lie outside the
+// tensor, so the copy writes them as zeros without reading memory and staged
+// rows are srow bytes apart.
+glm_status_t fused_tensor_map(glm_ctx *h, const void *X)
+{
+    if (h->box_rows == 0 || h->fx_map_ptr == X)
+        return GLM_OK;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode)
+        return GLM_ERR_CUDA;
+    const int row_bytes = h->d.ld * h->elem_bytes;
+    const cuuint64_t dims[2] = {(cuuint64_t)(row_bytes / 8), (cuuint64_t)h->d.n_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)(h->srow / 8), (cuuint32_t)h->box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap *map = reinterpret_cast<CUtensorMap *>(h->fx_map);
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(X), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return GLM_ERR_CUDA;
+    h->fx_map_ptr = X;
     return GLM_OK;
 }
 

@@ -90,19 +90,19 @@ struct FusedLayout {
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-__host__ __device__ inline FusedLayout fused_layout(int ld, int es, int epc, int tile_rows,
+__host__ __device__ inline FusedLayout fused_layout(int srow, int ld, int epc, int tile_rows,
                                                     int stages, int kc)
 {
     FusedLayout L;
     const int pce = (ld / epc) * epc;        // stored row length in elements
-    L.stage_bytes = tile_rows * ld * es;
+    L.stage_bytes = tile_rows * srow;        // srow: staged row stride in bytes
     const int red_bytes = kFusedThreads * kc * epc * 4;   // >= row groups x KC x used columns
     L.tiles_bytes = round_up(stages * L.stage_bytes > red_bytes ? stages * L.stage_bytes : red_bytes,
                              128);
     L.beta_off = L.tiles_bytes;
     L.rbuf_off = L.beta_off + round_up(kc * pce * 4, 16);
     L.bar_off = L.rbuf_off + round_up(tile_rows * kc * 4, 16);
-    L.total = L.bar_off + kMaxStages * 8 + 64;
+    L.total = L.bar_off + kMaxStages * 8 + 64 + 128;   // + slack to align the base to 128 B
     return L;
 }
 
@@ -121,7 +121,8 @@ __device__ __forceinline__ void tr_map(float eta, float yv, float &ell, float &r
 
 // --- the kernel --------------------------------------------------------------
 template <typename Tag, int KC, int SPLIT>
-__global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(FusedParams p)
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    fused_logpost_grad_kernel(const __grid_constant__ CUtensorMap xmap, FusedParams p)
 {
     using TR = XTraits<Tag>;
     constexpr int NT = kFusedThreads;
@@ -130,15 +131,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
     constexpr int EPC = TR::EPC;
     constexpr int ES = TR::ES;
 
-    extern __shared__ __align__(128) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    // tensor copies want 128-byte aligned destinations: align the base
+    uint8_t *smem = smem_raw + ((128u - (ptx::smem_u32(smem_raw) & 127u)) & 127u);
     const int P = p.P;
     const int ld = p.ld;
     const int PC = ld / EPC;               // chunks per stored row
     const int PCE = PC * EPC;
     const int PCU = (P + EPC - 1) / EPC;   // chunks that hold used columns
-    const int row_bytes = ld * ES;
+    const int row_bytes = ld * ES;         // row stride in global memory
+    const int srow = p.srow;               // row stride of the staged tile
+    const int SC = srow / 16;              // staged chunks per row
     const int T = p.tile_rows;             // rows per staged tile, a multiple of RB
-    const FusedLayout L = fused_layout(ld, ES, EPC, T, p.stages, KC);
+    const FusedLayout L = fused_layout(srow, ld, EPC, T, p.stages, KC);
     uint8_t *tiles = smem;
     float *beta_s = reinterpret_cast<float *>(smem + L.beta_off);
     float *rbuf = reinterpret_cast<float *>(smem + L.rbuf_off);
@@ -168,8 +173,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
     // Phase-1 thread -> (row, split part) mapping.
     // SPLIT <= 4: 8 consecutive lanes take 8 consecutive rows of the same part
     // (a contiguous run of chunks), so a quarter-warp's 16-byte loads fall in
-    // distinct bank groups when the row's chunk count is odd; for an even
-    // count each lane starts its walk at a rotated chunk.
+    // distinct bank groups when the staged chunk stride is odd (rows are
+    // staged padded to an odd stride whenever the tensor-copy path is on);
+    // for an even stride each lane starts its walk at a rotated chunk.
     // SPLIT == 32: one warp per row, lane l takes chunks l, l+32, ...; each
     // step reads 512 contiguous bytes.
     const int i8 = lane & 7;
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
         const int c_hi = (c_lo + seg) < PCU ? (c_lo + seg) : PCU;
         c_len = c_hi > c_lo ? c_hi - c_lo : 0;
         c_step = 1;
-        rot = ((PC & 1) == 0 && c_len > 0) ? (i8 % c_len) : 0;
+        rot = ((SC & 1) == 0 && c_len > 0) ? (i8 % c_len) : 0;
     }
 
     // Phase-2 mapping: thread -> (column chunk, row group).
@@ -233,6 +239,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
     // the programmatic dependency on the previous kernel resolves; every
     // other read waits for it.
     const uint64_t policy = ptx::policy_evict_first();
+    // Stage rows [row0, row0 + rows) into ring slot `slot`: one 1-D bulk copy
+    // of the dense rows, or ceil(rows / box_rows) 2-D tensor copies that
+    // write each row srow bytes apart (the extra chunk is zero fill).
+    auto issue_tile = [&](int slot, int64_t row0, int rows) {
+        uint8_t *dst = tiles + slot * L.stage_bytes;
+        if (p.box_rows == 0) {
+            const unsigned bytes = (unsigned)(rows * row_bytes);
+            ptx::mbar_arrive_expect_tx(&bars[slot], bytes);
+            ptx::bulk_g2s(dst, static_cast<const uint8_t *>(p.X) + row0 * (int64_t)row_bytes,
+                          bytes, &bars[slot], policy);
+        } else {
+            const int br = p.box_rows;
+            const int nb = (rows + br - 1) / br;
+            ptx::mbar_arrive_expect_tx(&bars[slot], (unsigned)(nb * br * srow));
+            for (int j = 0; j < nb; ++j)
+                ptx::tensor_g2s_2d(dst + j * br * srow, &xmap, 0, (int)(row0 + j * br),
+                                   &bars[slot], policy);
+        }
+    };
     auto issue_prologue = [&]() {
         if (tid != 0)
             return;
@@ -240,11 +265,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
         for (int t = 0; t < pre; ++t) {
             const int64_t row0 = r_begin + (int64_t)t * T;
             const int rows = (int)((r_end - row0) < T ? (r_end - row0) : T);
-            const unsigned bytes = (unsigned)(rows * row_bytes);
-            ptx::mbar_arrive_expect_tx(&bars[t], bytes);
-            ptx::bulk_g2s(tiles + t * L.stage_bytes,
-                          static_cast<const uint8_t *>(p.X) + row0 * (int64_t)row_bytes, bytes,
-                          &bars[t], policy);
+            issue_tile(t, row0, rows);
         }
     };
 
@@ -296,7 +317,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
             const bool valid = my_row < rows;
             const float yv = ycur[bi];
             if (valid) {
-                const uint8_t *xr = tile + my_row * row_bytes;
+                const uint8_t *xr = tile + my_row * srow;
                 int cs = rot;
 #pragma unroll 4
                 for (int it = 0; it < c_len; ++it) {
@@ -365,7 +386,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
 #pragma unroll 4
             for (int i = q2; i < rows; i += G2) {
                 float xv[EPC];
-                TR::load(xc + i * row_bytes, xv);
+                TR::load(xc + i * srow, xv);
                 float rk[KC];
                 if constexpr (KC % 4 == 0) {
 #pragma unroll
@@ -391,11 +412,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_logpost_grad_kernel(Fu
         if (tid == 0 && t + stages < ntiles) {
             const int64_t nrow0 = r_begin + (int64_t)(t + stages) * T;
             const int nrows = (int)((r_end - nrow0) < T ? (r_end - nrow0) : T);
-            const unsigned bytes = (unsigned)(nrows * row_bytes);
-            ptx::mbar_arrive_expect_tx(&bars[s], bytes);
-            ptx::bulk_g2s(tiles + s * L.stage_bytes,
-                          static_cast<const uint8_t *>(p.X) + nrow0 * (int64_t)row_bytes, bytes,
-                          &bars[s], policy);
+            issue_tile(s, nrow0, nrows);
         }
 #pragma unroll
         for (int bi = 0; bi < kMaxBatches; ++bi)
@@ -533,8 +550,10 @@ template <typename Tag>
 glm_status_t launch_fused_t(glm_ctx *h, const FusedParams &prm, int kc, cudaStream_t s)
 {
     using TR = XTraits<Tag>;
-    const FusedLayout L = fused_layout(prm.ld, TR::ES, TR::EPC, prm.tile_rows, prm.stages, kc);
-    void (*fn)(FusedParams) = nullptr;
+    const FusedLayout L = fused_layout(prm.srow, prm.ld, TR::EPC, prm.tile_rows, prm.stages, kc);
+    if (prm.box_rows > 0 && fused_tensor_map(h, prm.X) != GLM_OK)
+        return GLM_ERR_CUDA;
+    void (*fn)(const CUtensorMap, FusedParams) = nullptr;
 #define GLM_PICK(KCV, SP)                                                   \
     if (kc == KCV && h->split == SP)                                        \
         fn = fused_logpost_grad_kernel<Tag, KCV, SP>;
@@ -559,7 +578,8 @@ glm_status_t launch_fused_t(glm_ctx *h, const FusedParams &prm, int kc, cudaStre
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = h->use_pdl ? 1 : 0;
-    if (cudaLaunchKernelEx(&cfg, fn, prm) != cudaSuccess)
+    const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(h->fx_map);
+    if (cudaLaunchKernelEx(&cfg, fn, *map, prm) != cudaSuccess)
         return GLM_ERR_CUDA;
     return GLM_OK;
 }

@@ -3,6 +3,8 @@
 // copies) shared by the kernels. Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -62,6 +64,8 @@ struct FusedParams {
     uint8_t *accept;           // K or null
     double *logpost;           // K or null
     int early_prefetch;        // stream X/y before the launch dependency resolves
+    int srow;                  // staged row stride in shared memory, bytes
+    int box_rows;              // > 0: rows arrive by 3-D tensor copies of this many rows
 };
 
 // Kernel parameter block of the grouped (hierarchical-Bayes) pass.
@@ -105,6 +109,13 @@ struct glm_ctx {
     int smem_bytes;
     int kc_max;                 // largest KC instantiation usable for this xtype
     int use_pdl;                // launch with programmatic stream serialization
+    // Rows whose 16-byte chunk count is even are staged one zero chunk wider
+    // (odd chunk stride: a quarter-warp reading 8 consecutive rows at the
+    // same column hits 8 distinct bank groups), through a 3-D tensor map.
+    int srow;                   // staged row stride in bytes
+    int box_rows;               // rows per tensor copy (0: dense 1-D bulk copies)
+    alignas(64) unsigned char fx_map[128];   // CUtensorMap of the last X seen
+    const void *fx_map_ptr;
     // workspace
     void *ws;                   // one device allocation
     size_t ws_bytes;
@@ -149,6 +160,11 @@ glm_status_t launch_wait_timeout(glm_ctx *h, int spin_limit, cudaStream_t s);
 // the same kernel concurrently with different sizes cannot lower it between
 // another thread's set and launch. Done once per (kernel, device).
 cudaError_t allow_max_dynamic_smem(const void *fn);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); nullptr if unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+// Encode (or reuse) the fused path's padded-row tensor map for X.
+glm_status_t fused_tensor_map(glm_ctx *h, const void *X);
 glm_status_t grouped_configure(glm_ctx *h);
 size_t tc_workspace_bytes(const glm_ctx *h);
 glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
@@ -232,6 +248,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
         "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// Two-dimensional tiled tensor copy global -> shared (coordinates innermost
+// first), completing the box's bytes on `bar`. The box lands densely in
+// shared memory; elements outside the tensor are written as zeros and are
+// not read from memory.
+__device__ __forceinline__ void tensor_g2s_2d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                              uint64_t *bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 

@@ -142,6 +142,8 @@ extern "C" glm_status_t glm_logpost_grad_noalloc(const void *X, const float *x_s
         prm.K = kk;
         prm.stages = c.stages;
         prm.tile_rows = c.tile_rows;
+        prm.srow = c.srow;
+        prm.box_rows = c.box_rows;
         prm.inv_s2 = 1.0 / s2;
         prm.prior_const = 0.5 * (double)p * std::log(2.0 * M_PI * s2);
         prm.acc = c.acc;

@@ -646,16 +646,9 @@ static glm_status_t tc_tensor_map(glm_ctx *h, const void *X)
 {
     if (h->tc_map_ptr == X)
         return GLM_OK;
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        cudaDriverEntryPointQueryResult q;
-        void *fn = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                             &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return GLM_ERR_CUDA;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode)
+        return GLM_ERR_CUDA;
     const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld, (cuuint64_t)h->d.n_rows};
     const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld * 2};
     const cuuint32_t box[2] = {64, (cuuint32_t)kTcRows};
