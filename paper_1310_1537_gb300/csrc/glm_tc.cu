@@ -18,11 +18,22 @@
 // while X stays in 2-byte storage. Per-CTA partials are combined by a second
 // kernel in a fixed order (deterministic).
 //
+// FP8 E4M3 storage: every E4M3 value is exactly an FP16 normal, so two
+// converter warps turn each staged E4M3 tile into FP16 in the same swizzled
+// layout (one cvt per pair of values) and the MMAs run with FP16 operands;
+// beta and r are split into FP16 hi + lo terms. The column scales fold into
+// the coefficients (eta = q . (s o beta)) and into the final combine
+// (g_j = s_j sum_n q_nj r_n); a power-of-two factor per vector keeps s o beta
+// in FP16 range and is divided out of eta exactly.
+//
 // Warp roles: warp 0 issues TMA loads, warp 1 allocates tensor memory and one
-// of its threads issues the MMAs, warps 2..9 run the epilogue (and first load
-// beta into tensor memory). Every wait is bounded.
+// of its threads issues the MMAs, warps 2..17 run the epilogue (and first load
+// beta into tensor memory), warps 18..19 convert FP8 tiles (FP8 storage only).
+// Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -37,7 +48,10 @@ constexpr int kTcEpiGroups = kTcEpiWarps / 4;       // warps per tensor-memory l
 constexpr int kTcEpiCols = 128 / kTcEpiGroups;      // D1 columns (tile rows) per warp
 constexpr int kTcEpiRows = kTcEpiCols / 2;          // rows per thread
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
+constexpr int kTcConvWarps = 2;                     // FP8 tile converters
+constexpr int kTcThreadsFp8 = kTcThreads + 32 * kTcConvWarps;
 constexpr int kTcMaxStages = 4;
+constexpr int kTcMaxRawStages = 2;
 constexpr int kTcMaxP = 256;
 constexpr int kTcMaxKB = 64;
 constexpr int kTcTmemCols = 512;
@@ -51,6 +65,8 @@ struct TcParams {
     int PA;                     // 64-column atoms of the tile
     int MB;                     // 128-column blocks of P for MMA2
     int stages;
+    int raw_stages;             // FP8 storage: staged E4M3 tiles
+    const float *x_scale;       // FP8 storage: P column scales
     int y_al4;                  // y is 4-byte aligned: labels read as words
     double *part_f;             // grid x 64
     float *part_g;              // grid x 64 x (MB*128)
@@ -76,11 +92,12 @@ __device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
-// kind::f16 instruction descriptor: D f32, A and B bf16, M=128, N=n.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n, int a_mn, int b_mn)
+// kind::f16 instruction descriptor: D f32, A and B both bf16 (ab_type 1) or
+// both f16 (ab_type 0), M=128, N=n.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int n, int a_mn, int b_mn, uint32_t ab_type)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+    return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)a_mn << 15) |
+           ((uint32_t)b_mn << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -206,6 +223,43 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
+__device__ __forceinline__ uint32_t pack_f16(float a, float b)
+{
+    __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Two-term split of v in the operand type: hi = round(v), lo = round(v - hi).
+template <bool F16>
+__device__ __forceinline__ void split2(float v, float &hi, float &lo)
+{
+    if constexpr (F16) {
+        hi = __half2float(__float2half_rn(v));
+    } else {
+        hi = __bfloat162float(__float2bfloat16_rn(v));
+    }
+    lo = v - hi;
+}
+
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    if constexpr (F16)
+        return pack_f16(a, b);
+    else
+        return pack_bf16(a, b);
+}
+
+// Four E4M3 codes (one 32-bit word) to four FP16 values (two 32-bit words),
+// exactly: E4M3 values are all FP16 normals or zero.
+__device__ __forceinline__ void e4m3x4_to_f16(uint32_t w, uint32_t &lo, uint32_t &hi)
+{
+    __half2_raw a = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w & 0xFFFFu), __NV_E4M3);
+    __half2_raw b = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w >> 16), __NV_E4M3);
+    lo = (uint32_t)a.x | ((uint32_t)a.y << 16);
+    hi = (uint32_t)b.x | ((uint32_t)b.y << 16);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -218,23 +272,27 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // Shared-memory layout of the tensor-core kernel (1024-byte aligned parts).
 struct TcLayout {
-    int x_stage;    // PA * 16 KB
+    int x_stage;    // PA * 16 KB (bf16 / f16 operand tile, 128B swizzle)
     int x_off;
     int r_off;      // R tile: 2 regions of (128 rows x 128 B)
-    int bar_off;
+    int raw_stage;  // FP8 storage: 128 rows x (PA * 64 + 16) bytes
+    int raw_off;
+    int bar_off;    // barriers, tensor-memory slot, per-vector scales
     int sf_off;     // 4 x 64 doubles (inside the R tile, used after the last MMA)
     int total;      // including 1 KB alignment slack
 };
 
-__host__ __device__ inline TcLayout tc_layout(int PA, int stages)
+__host__ __device__ inline TcLayout tc_layout(int PA, int stages, int raw_stages)
 {
     TcLayout L;
     L.x_stage = PA * 16384;
     L.x_off = 0;
     L.r_off = stages * L.x_stage;
-    L.bar_off = L.r_off + 2 * 16384;
+    L.raw_stage = raw_stages > 0 ? (kTcRows * (PA * 64 + 16) + 1023) / 1024 * 1024 : 0;
+    L.raw_off = L.r_off + 2 * 16384;
+    L.bar_off = L.raw_off + raw_stages * L.raw_stage;
     L.sf_off = L.r_off;
-    L.total = L.bar_off + 256 + 1024;
+    L.total = L.bar_off + 512 + 1024;
     return L;
 }
 
@@ -244,20 +302,25 @@ constexpr int kTcB1Col = 0;
 constexpr int kTcD1Col = 128;
 constexpr int kTcD2Col = 256;
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <bool FP8>
+__global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
     tc_logpost_grad_kernel(const __grid_constant__ CUtensorMap tmap, TcParams p)
 {
-    constexpr uint32_t ID1 = tc::idesc_bf16(128, 0, 0);
-    constexpr uint32_t ID2 = tc::idesc_bf16(128, 1, 1);
+    // operands: bf16 for BF16 storage, f16 for FP8 storage (A and B alike)
+    constexpr uint32_t AB = FP8 ? 0u : 1u;
+    constexpr uint32_t ID1 = tc::idesc_f16kind(128, 0, 0, AB);
+    constexpr uint32_t ID2 = tc::idesc_f16kind(128, 1, 1, AB);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int PA = p.PA;
     const int MB = p.MB;
     const int stages = p.stages;
-    const TcLayout L = tc_layout(PA, stages);
+    const int RS = p.raw_stages;
+    const TcLayout L = tc_layout(PA, stages, FP8 ? RS : 0);
     uint8_t *xs = smem + L.x_off;
     uint8_t *rb = smem + L.r_off;
+    uint8_t *raw = smem + L.raw_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bar_off);
     uint64_t *x_full = bars;                    // [stages]
     uint64_t *x_empty = bars + kTcMaxStages;    // [stages]
@@ -266,7 +329,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t *r_full = d1_empty + 1;
     uint64_t *r_empty = r_full + 1;
     uint64_t *d2_done = r_empty + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d2_done + 1);
+    uint64_t *raw_full = d2_done + 1;           // [kTcMaxRawStages]
+    uint64_t *raw_empty = raw_full + kTcMaxRawStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw_empty + kTcMaxRawStages);
+    float *vscale = reinterpret_cast<float *>(smem + L.bar_off + 256);   // [64]: 2^-e_k
     double *sf = reinterpret_cast<double *>(smem + L.sf_off);
     __shared__ int s_abort;
 
@@ -277,11 +343,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int b = blockIdx.x;
     const int64_t ntiles_all = (p.N + kTcRows - 1) / kTcRows;
     const int nt = (int)(ntiles_all > b ? (ntiles_all - b + grid - 1) / grid : 0);
+    const int raw_row = PA * 64 + 16;           // staged E4M3 row: one zero chunk wider
 
     if (tid == 0) {
         for (int s = 0; s < kTcMaxStages; ++s) {
-            ptx::mbar_init(&x_full[s], 1);
+            ptx::mbar_init(&x_full[s], FP8 ? kTcConvWarps : 1);
             ptx::mbar_init(&x_empty[s], 1);
+        }
+        for (int s = 0; s < kTcMaxRawStages; ++s) {
+            ptx::mbar_init(&raw_full[s], 1);
+            ptx::mbar_init(&raw_empty[s], kTcConvWarps);
         }
         ptx::mbar_init(d1_full, 1);
         ptx::mbar_init(d1_empty, kTcEpiWarps);
@@ -305,13 +376,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // beta into tensor memory: lane n = 2k + part holds the bf16 hi (part 0) or
-    // lo (part 1) term of beta_k, two columns of beta per 32-bit cell
+    // beta into tensor memory: lane n = 2k + part holds the hi (part 0) or lo
+    // (part 1) term of beta_k, two columns of beta per 32-bit cell. FP8
+    // storage: the coefficients are s_j beta_kj times 2^e_k, with e_k the
+    // power of two that brings max_j |s_j beta_kj| just under 2^14.
     if (warp >= 2 && warp < 6) {
         const int q = warp & 3;
         const int n = q * 32 + lane;
         const int k = n >> 1;
         const int part = n & 1;
+        float scale = 1.0f;
+        if constexpr (FP8) {
+            float m = 0.0f;
+            if (k < p.kk)
+                for (int col = 0; col < p.P; ++col)
+                    m = fmaxf(m, fabsf(p.beta[(size_t)k * p.P + col] * p.x_scale[col]));
+            int e = 0;
+            if (m > 0.0f) {
+                int ex;
+                frexpf(m, &ex);                 // m < 2^ex
+                e = 14 - ex;
+                e = e < -100 ? -100 : (e > 100 ? 100 : e);
+            }
+            scale = ldexpf(1.0f, e);
+            if (part == 0 && k < 64)
+                vscale[k] = ldexpf(1.0f, -e);
+        }
         for (int cb = 0; cb < PA * 32; cb += 32) {
             uint32_t r[32];
 #pragma unroll
@@ -321,12 +411,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int e = 0; e < 2; ++e) {
                     const int col = 2 * (cb + j) + e;
                     float v = 0.0f;
-                    if (k < p.kk && col < p.P)
+                    if (k < p.kk && col < p.P) {
                         v = p.beta[(size_t)k * p.P + col];
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                    v2[e] = part ? v - __bfloat162float(hi) : v;
+                        if constexpr (FP8)
+                            v = v * p.x_scale[col] * scale;
+                    }
+                    float hi, lo;
+                    tc::split2<FP8>(v, hi, lo);
+                    v2[e] = part ? lo : hi;
                 }
-                r[j] = tc::pack_bf16(v2[0], v2[1]);
+                r[j] = tc::pack2<FP8>(v2[0], v2[1]);
             }
             tc::tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + kTcB1Col + cb, r);
         }
@@ -340,19 +434,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 0) {
         // ---- TMA producer ------------------------------------------------------------
         if (lane == 0) {
-            const unsigned bytes = (unsigned)(PA * 16384);
-            for (int i = 0; i < nt; ++i) {
-                const int s = i % stages;
-                const int use = i / stages;
-                if (use > 0 && !ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
-                    atomicOr(p.status, kDevTimeout);
-                    s_abort = 1;
-                    break;
+            if constexpr (!FP8) {
+                const unsigned bytes = (unsigned)(PA * 16384);
+                for (int i = 0; i < nt; ++i) {
+                    const int s = i % stages;
+                    const int use = i / stages;
+                    if (use > 0 && !ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
+                        atomicOr(p.status, kDevTimeout);
+                        s_abort = 1;
+                        break;
+                    }
+                    const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kTcRows);
+                    ptx::mbar_arrive_expect_tx(&x_full[s], bytes);
+                    for (int a = 0; a < PA; ++a)
+                        tc::tma_load_2d(xs + s * L.x_stage + a * 16384, &tmap, a * 64, row0, &x_full[s]);
                 }
-                const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kTcRows);
-                ptx::mbar_arrive_expect_tx(&x_full[s], bytes);
-                for (int a = 0; a < PA; ++a)
-                    tc::tma_load_2d(xs + s * L.x_stage + a * 16384, &tmap, a * 64, row0, &x_full[s]);
+            } else {
+                // E4M3 rows into the raw ring, each one chunk wider than the row
+                // (the extra chunk is outside the tensor: zero fill)
+                const unsigned bytes = (unsigned)(kTcRows * raw_row);
+                for (int i = 0; i < nt; ++i) {
+                    const int s = i % RS;
+                    const int use = i / RS;
+                    if (use > 0 && !ptx::mbar_wait_bounded(&raw_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
+                        atomicOr(p.status, kDevTimeout);
+                        s_abort = 1;
+                        break;
+                    }
+                    const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kTcRows);
+                    ptx::mbar_arrive_expect_tx(&raw_full[s], bytes);
+                    tc::tma_load_2d(raw + s * L.raw_stage, &tmap, 0, row0, &raw_full[s]);
+                }
             }
         }
     } else if (warp == 1) {
@@ -403,6 +515,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (nt > 0)
                 tc::commit(d2_done);
         }
+    } else if (FP8 && warp >= 2 + kTcEpiWarps) {
+        // ---- E4M3 -> FP16 converters ----------------------------------------------------
+        // thread ct takes tile rows ct, ct + 64: reads 16-byte chunks of its raw
+        // row (odd chunk stride: 8 consecutive rows hit distinct bank groups) and
+        // writes two 16-byte FP16 chunks into the 128B-swizzled operand tile
+        const int ct = (warp - 2 - kTcEpiWarps) * 32 + lane;
+        bool ok = true;
+        for (int i = 0; i < nt; ++i) {
+            const int rs = i % RS;
+            const int s = i % stages;
+            ok = ptx::mbar_wait_bounded(&raw_full[rs], (unsigned)(i / RS) & 1u, kSpinLimit);
+            if (ok && i >= stages)
+                ok = ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(i / stages - 1) & 1u, kSpinLimit);
+            if (!ok)
+                break;
+            const uint8_t *src_t = raw + rs * L.raw_stage;
+            uint8_t *dst_t = xs + s * L.x_stage;
+#pragma unroll
+            for (int h = 0; h < kTcRows / (32 * kTcConvWarps); ++h) {
+                const int r = ct + h * 32 * kTcConvWarps;
+                const uint8_t *src = src_t + r * raw_row;
+                for (int c = 0; c < PA * 4; ++c) {
+                    const uint4 a = *reinterpret_cast<const uint4 *>(src + c * 16);
+                    uint4 o0, o1;
+                    tc::e4m3x4_to_f16(a.x, o0.x, o0.y);
+                    tc::e4m3x4_to_f16(a.y, o0.z, o0.w);
+                    tc::e4m3x4_to_f16(a.z, o1.x, o1.y);
+                    tc::e4m3x4_to_f16(a.w, o1.z, o1.w);
+                    // FP16 columns 16c .. 16c + 15: atom c / 4, chunks 2 (c % 4) and +1
+                    uint8_t *atom = dst_t + (c >> 2) * 16384 + r * 128;
+                    const uint32_t ch = (uint32_t)((c & 3) * 2);
+                    *reinterpret_cast<uint4 *>(atom + ((ch ^ (uint32_t)(r & 7)) << 4)) = o0;
+                    *reinterpret_cast<uint4 *>(atom + (((ch + 1) ^ (uint32_t)(r & 7)) << 4)) = o1;
+                }
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                ptx::mbar_arrive(&raw_empty[rs]);
+                ptx::mbar_arrive(&x_full[s]);
+            }
+        }
+        if (!ok) {
+            atomicOr(p.status, kDevTimeout);
+            s_abort = 1;
+        }
     } else {
         // ---- epilogue ---------------------------------------------------------------------
         constexpr int CW = kTcEpiCols;
@@ -414,6 +572,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int part = n & 1;                 // 0: beta_hi lane, 1: beta_lo lane
         const bool active = k < p.kk;
         const int tb = CW * hh + RT * part;     // this thread's RT rows
+        float vs = 1.0f;                        // 2^-e_k (FP8 storage)
+        if constexpr (FP8)
+            vs = vscale[k];
         float facc = 0.0f;
         uint32_t yw[RT / 4], yn[RT / 4];
         auto load_y = [&](int i, uint32_t *dst) {
@@ -461,6 +622,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int j = 0; j < RT; ++j) {
                 const float send = part ? v[j] : v[RT + j];
                 mine[j] = (part ? v[RT + j] : v[j]) + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
+                if constexpr (FP8)
+                    mine[j] *= vs;
             }
             if (nvalid == RT) {
 #pragma unroll
@@ -469,9 +632,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     float ell, r;
                     tc::tr_fast(mine[j], yv, ell, r);
                     facc += ell;
-                    const __nv_bfloat16 rh = __float2bfloat16_rn(r);
-                    const float rhf = __bfloat162float(rh);
-                    w[j] = tc::pack_bf16(rhf, r - rhf);
+                    float rh, rl;
+                    tc::split2<FP8>(r, rh, rl);
+                    w[j] = tc::pack2<FP8>(rh, rl);
                 }
             } else {
 #pragma unroll
@@ -482,9 +645,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const bool in = j < nvalid;
                     facc += in ? ell : 0.0f;
                     r = in ? r : 0.0f;
-                    const __nv_bfloat16 rh = __float2bfloat16_rn(r);
-                    const float rhf = __bfloat162float(rh);
-                    w[j] = tc::pack_bf16(rhf, r - rhf);
+                    float rh, rl;
+                    tc::split2<FP8>(r, rh, rl);
+                    w[j] = tc::pack2<FP8>(rh, rl);
                 }
             }
             if (i >= 1 && !ptx::mbar_wait_bounded(r_empty, (unsigned)(i - 1) & 1u, kSpinLimit)) {
@@ -630,18 +793,29 @@ __global__ void __launch_bounds__(32 * kTcRedWarps)
 
 bool tc_supported(const glm_ctx *h)
 {
-    return h->d.xtype == GLM_X_BF16 && h->d.p <= kTcMaxP && h->d.k_max >= 16 &&
-           std::getenv("GLM_NO_TC") == nullptr;
+    return (h->d.xtype == GLM_X_BF16 || h->d.xtype == GLM_X_FP8E4M3) && h->d.p <= kTcMaxP &&
+           h->d.k_max >= 16 && std::getenv("GLM_NO_TC") == nullptr;
 }
 
-static int tc_stages(int PA)
+// Ring depths that fit: operand-tile stages (2..4) and, for FP8 storage,
+// staged E4M3 tiles (2, else 1). Returns false if not even two operand stages fit.
+static bool tc_stages(int PA, bool fp8, int *stages, int *raw_stages)
 {
-    int st = kTcMaxStages;
-    while (st >= 2 && tc_layout(PA, st).total > kSmemDynamicBudget)
-        --st;
-    return st;
+    for (int st = kTcMaxStages; st >= 2; --st) {
+        for (int rs = fp8 ? kTcMaxRawStages : 0; rs >= (fp8 ? 1 : 0); --rs) {
+            if (tc_layout(PA, st, rs).total <= kSmemDynamicBudget) {
+                *stages = st;
+                *raw_stages = rs;
+                return true;
+            }
+        }
+    }
+    return false;
 }
 
+// BF16: 64-column boxes with the 128B swizzle, loaded straight into the MMA
+// layout. FP8: the E4M3 rows as 16-bit pairs in one box one chunk wider
+// than the padded row (the extra chunk is outside the tensor: zero fill).
 static glm_status_t tc_tensor_map(glm_ctx *h, const void *X)
 {
     if (h->tc_map_ptr == X)
@@ -649,15 +823,25 @@ static glm_status_t tc_tensor_map(glm_ctx *h, const void *X)
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode)
         return GLM_ERR_CUDA;
-    const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld, (cuuint64_t)h->d.n_rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld * 2};
-    const cuuint32_t box[2] = {64, (cuuint32_t)kTcRows};
-    const cuuint32_t estr[2] = {1, 1};
     CUtensorMap *map = reinterpret_cast<CUtensorMap *>(h->tc_map);
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(X), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r;
+    if (h->d.xtype == GLM_X_FP8E4M3) {
+        const int PA = (h->d.p + 63) / 64;
+        const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld / 2, (cuuint64_t)h->d.n_rows};
+        const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld};
+        const cuuint32_t box[2] = {(cuuint32_t)(PA * 32 + 8), (cuuint32_t)kTcRows};
+        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(X), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld, (cuuint64_t)h->d.n_rows};
+        const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld * 2};
+        const cuuint32_t box[2] = {64, (cuuint32_t)kTcRows};
+        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(X), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS)
         return GLM_ERR_CUDA;
     h->tc_map_ptr = X;
@@ -683,6 +867,10 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
     const int MB = (P + 127) / 128;
     const double s2 = h->d.prior_sigma * h->d.prior_sigma;
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(h->tc_map);
+    const bool fp8 = h->d.xtype == GLM_X_FP8E4M3;
+    int stages = 0, raw_stages = 0;
+    if (!tc_stages(PA, fp8, &stages, &raw_stages))
+        return GLM_ERR_UNSUPPORTED;
     for (int k0 = 0; k0 < K; k0 += kTcMaxKB) {
         const int kk = (K - k0) < kTcMaxKB ? (K - k0) : kTcMaxKB;
         const int KB = kTcMaxKB;
@@ -696,19 +884,19 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         prm.kk = kk;
         prm.PA = PA;
         prm.MB = MB;
-        prm.stages = tc_stages(PA);
-        if (prm.stages < 2)
-            return GLM_ERR_UNSUPPORTED;
+        prm.stages = stages;
+        prm.raw_stages = raw_stages;
+        prm.x_scale = x_scale;
         prm.part_f = h->tc_part_f;
         prm.part_g = h->tc_part_g;
         prm.status = h->status;
-        auto fn = &tc_logpost_grad_kernel;
-        const TcLayout L = tc_layout(PA, prm.stages);
+        auto fn = fp8 ? &tc_logpost_grad_kernel<true> : &tc_logpost_grad_kernel<false>;
+        const TcLayout L = tc_layout(PA, prm.stages, prm.raw_stages);
         if (allow_max_dynamic_smem(reinterpret_cast<const void *>(fn)) != cudaSuccess)
             return GLM_ERR_CUDA;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)h->sm_count);
-        cfg.blockDim = dim3(kTcThreads);
+        cfg.blockDim = dim3(fp8 ? kTcThreadsFp8 : kTcThreads);
         cfg.dynamicSmemBytes = (size_t)L.total;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
