@@ -48,7 +48,7 @@ constexpr int kTcEpiGroups = kTcEpiWarps / 4;       // warps per tensor-memory l
 constexpr int kTcEpiCols = 128 / kTcEpiGroups;      // D1 columns (tile rows) per warp
 constexpr int kTcEpiRows = kTcEpiCols / 2;          // rows per thread
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
-constexpr int kTcConvWarps = 2;                     // FP8 tile converters
+constexpr int kTcConvWarps = 4;                     // FP8 tile converters
 constexpr int kTcThreadsFp8 = kTcThreads + 32 * kTcConvWarps;
 constexpr int kTcMaxStages = 4;
 constexpr int kTcMaxRawStages = 2;
@@ -254,18 +254,10 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
 // exactly: E4M3 values are all FP16 normals or zero.
 __device__ __forceinline__ void e4m3x4_to_f16(uint32_t w, uint32_t &lo, uint32_t &hi)
 {
-    __half2_raw a = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w & 0xFFFFu), __NV_E4M3);
-    __half2_raw b = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w >> 16), __NV_E4M3);
-    lo = (uint32_t)a.x | ((uint32_t)a.y << 16);
-    hi = (uint32_t)b.x | ((uint32_t)b.y << 16);
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1)
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
-    return v;
+    asm("{\n\t.reg .b16 a, b;\n\tmov.b32 {a, b}, %2;\n\t"
+        "cvt.rn.f16x2.e4m3x2 %0, a;\n\tcvt.rn.f16x2.e4m3x2 %1, b;\n\t}"
+        : "=r"(lo), "=r"(hi)
+        : "r"(w));
 }
 
 }  // namespace tc
@@ -532,22 +524,35 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                 break;
             const uint8_t *src_t = raw + rs * L.raw_stage;
             uint8_t *dst_t = xs + s * L.x_stage;
-#pragma unroll
+            // eight 16-byte loads in flight before converting (PA * 4 chunks
+            // per row, a multiple of 4: the tail group is guarded)
             for (int h = 0; h < kTcRows / (32 * kTcConvWarps); ++h) {
                 const int r = ct + h * 32 * kTcConvWarps;
                 const uint8_t *src = src_t + r * raw_row;
-                for (int c = 0; c < PA * 4; ++c) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(src + c * 16);
-                    uint4 o0, o1;
-                    tc::e4m3x4_to_f16(a.x, o0.x, o0.y);
-                    tc::e4m3x4_to_f16(a.y, o0.z, o0.w);
-                    tc::e4m3x4_to_f16(a.z, o1.x, o1.y);
-                    tc::e4m3x4_to_f16(a.w, o1.z, o1.w);
-                    // FP16 columns 16c .. 16c + 15: atom c / 4, chunks 2 (c % 4) and +1
-                    uint8_t *atom = dst_t + (c >> 2) * 16384 + r * 128;
-                    const uint32_t ch = (uint32_t)((c & 3) * 2);
-                    *reinterpret_cast<uint4 *>(atom + ((ch ^ (uint32_t)(r & 7)) << 4)) = o0;
-                    *reinterpret_cast<uint4 *>(atom + (((ch + 1) ^ (uint32_t)(r & 7)) << 4)) = o1;
+                uint8_t *dst_r = dst_t + r * 128;
+                const uint32_t rx = (uint32_t)(r & 7);
+                for (int c0 = 0; c0 < PA * 4; c0 += 8) {
+                    uint4 a[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (c0 + u < PA * 4)
+                            a[u] = *reinterpret_cast<const uint4 *>(src + (c0 + u) * 16);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = c0 + u;
+                        if (c < PA * 4) {
+                            uint4 o0, o1;
+                            tc::e4m3x4_to_f16(a[u].x, o0.x, o0.y);
+                            tc::e4m3x4_to_f16(a[u].y, o0.z, o0.w);
+                            tc::e4m3x4_to_f16(a[u].z, o1.x, o1.y);
+                            tc::e4m3x4_to_f16(a[u].w, o1.z, o1.w);
+                            // FP16 columns 16c .. 16c + 15: atom c / 4, chunks 2 (c % 4) and +1
+                            uint8_t *atom = dst_r + (c >> 2) * 16384;
+                            const uint32_t ch = (uint32_t)((c & 3) * 2);
+                            *reinterpret_cast<uint4 *>(atom + ((ch ^ rx) << 4)) = o0;
+                            *reinterpret_cast<uint4 *>(atom + (((ch + 1) ^ rx) << 4)) = o1;
+                        }
+                    }
                 }
             }
             ptx::fence_proxy_async_smem();
@@ -736,14 +741,16 @@ __global__ void __launch_bounds__(32 * kTcRedWarps)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     if ((int)blockIdx.x < ng) {
-        __shared__ double part_sum[kTcRedWarps][32];
+        __shared__ float part_sum[kTcRedWarps][32];
         const int cpk = (P + 31) / 32;                 // column blocks per vector
         const int k = blockIdx.x / cpk;
         const int jj = (blockIdx.x - k * cpk) * 32 + lane;
         const int per = (parts + kTcRedWarps - 1) / kTcRedWarps;
         const int c0 = warp * per;
         const int c1 = (c0 + per) < parts ? (c0 + per) : parts;
-        double v = 0.0;
+        // FP32 sums in a fixed order (FP64 throughput is low on this part;
+        // the partials are FP32 tensor-memory sums already)
+        float v = 0.0f;
         if (jj < P) {
             const float *src = part_g + (size_t)k * PP + jj;
             const size_t stride = (size_t)KB * PP;
@@ -754,18 +761,18 @@ __global__ void __launch_bounds__(32 * kTcRedWarps)
                     buf[u] = (cb + u < c1) ? __ldg(src + (size_t)(cb + u) * stride) : 0.0f;
 #pragma unroll
                 for (int u = 0; u < 32; ++u)
-                    v += (double)buf[u];
+                    v += buf[u];
             }
         }
         part_sum[warp][lane] = v;
         __syncthreads();
         if (warp == 0 && jj < P) {
-            double t = 0.0;
+            float t = 0.0f;
 #pragma unroll
             for (int w = 0; w < kTcRedWarps; ++w)
                 t += part_sum[w][lane];
-            const double sc = x_scale ? (double)x_scale[jj] : 1.0;
-            g_out[(size_t)k * P + jj] = (float)(sc * t - (double)beta[(size_t)k * P + jj] * inv_s2);
+            const float sc = x_scale ? x_scale[jj] : 1.0f;
+            g_out[(size_t)k * P + jj] = fmaf(sc, t, -beta[(size_t)k * P + jj] * (float)inv_s2);
         }
         return;
     }

@@ -171,3 +171,33 @@ def test_tc_fp8_batched_workload_full_size_sampled():
         ef, eg = assert_close(f[kk:kk + 1], g[kk:kk + 1], f_o, g_o, f_rtol=RTOL, g_rtol=RTOL,
                               what=f"fp8 full size k={kk}")
         print(f"fp8 k={kk}: f {ef:.2e} g {eg:.2e}")
+
+
+def test_tc_fp8_subnormal_codes():
+    """Columns whose values sit far below their column maximum quantise to
+    E4M3 subnormal codes (|q| < 2^-6); their FP16 images are exact and must
+    enter both contractions unchanged."""
+    n, p, k = 6000, 32, 16
+    d = synth.make_glm(n, p, 71, dtype=np.float32)
+    X = d.X.copy()
+    rng = np.random.default_rng(72)
+    for j in (3, 7, 11):
+        X[:, j] = 3e-4 * rng.standard_normal(n)
+        X[0, j] = 10.0
+    ld = synth.padded_ld(p, 1)
+    Q, sc = oracle.quantize_e4m3(X, p, ld)
+    codes = Q[1:, [3, 7, 11]]
+    subnormal = ((codes & 0x78) == 0) & ((codes & 0x07) != 0)
+    assert subnormal.mean() > 0.5, subnormal.mean()
+    Xr = oracle.dequantize_e4m3(Q, sc)
+    B = (d.beta_star[None, :] + 0.05 * rng.standard_normal((k, p))).astype(np.float32)
+    B[:, [3, 7, 11]] = 500.0 * rng.standard_normal((k, 3))   # make those columns matter
+    h = _tc_fp8_handle(Q, sc, d.y, p, k)
+    f, g = h.eval(B)
+    f_o, g_o = oracle.logpost_grad(Xr, d.y, B.astype(np.float64), p=p)
+    assert_close(f, g, f_o, g_o, f_rtol=RTOL, g_rtol=RTOL, what="tc fp8 subnormal codes")
+    # the subnormal columns of g on their own
+    cols = [3, 7, 11]
+    num = np.linalg.norm(g[:, cols] - g_o[:, cols], axis=1)
+    den = np.linalg.norm(g_o[:, cols], axis=1)
+    assert (num <= 1e-4 * den + 1e-6 * np.linalg.norm(g_o, axis=1)).all()
