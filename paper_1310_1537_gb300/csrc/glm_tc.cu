@@ -51,7 +51,8 @@ constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTcConvWarps = 4;                     // FP8 tile converters
 constexpr int kTcThreadsFp8 = kTcThreads + 32 * kTcConvWarps;
 constexpr int kTcMaxStages = 4;
-constexpr int kTcMaxRawStages = 2;
+constexpr int kTcRawRows = 64;                      // rows per staged E4M3 slot (half a tile)
+constexpr int kTcMaxRawStages = 3;
 constexpr int kTcMaxP = 256;
 constexpr int kTcMaxKB = 64;
 constexpr int kTcTmemCols = 512;
@@ -65,7 +66,7 @@ struct TcParams {
     int PA;                     // 64-column atoms of the tile
     int MB;                     // 128-column blocks of P for MMA2
     int stages;
-    int raw_stages;             // FP8 storage: staged E4M3 tiles
+    int raw_stages;             // FP8 storage: staged E4M3 half tiles (64 rows)
     const float *x_scale;       // FP8 storage: P column scales
     int y_al4;                  // y is 4-byte aligned: labels read as words
     double *part_f;             // grid x 64
@@ -267,7 +268,7 @@ struct TcLayout {
     int x_stage;    // PA * 16 KB (bf16 / f16 operand tile, 128B swizzle)
     int x_off;
     int r_off;      // R tile: 2 regions of (128 rows x 128 B)
-    int raw_stage;  // FP8 storage: 128 rows x (PA * 64 + 16) bytes
+    int raw_stage;  // FP8 storage: 64 rows x (PA * 64 + 16) bytes
     int raw_off;
     int bar_off;    // barriers, tensor-memory slot, per-vector scales
     int sf_off;     // 4 x 64 doubles (inside the R tile, used after the last MMA)
@@ -280,7 +281,7 @@ __host__ __device__ inline TcLayout tc_layout(int PA, int stages, int raw_stages
     L.x_stage = PA * 16384;
     L.x_off = 0;
     L.r_off = stages * L.x_stage;
-    L.raw_stage = raw_stages > 0 ? (kTcRows * (PA * 64 + 16) + 1023) / 1024 * 1024 : 0;
+    L.raw_stage = raw_stages > 0 ? (kTcRawRows * (PA * 64 + 16) + 1023) / 1024 * 1024 : 0;
     L.raw_off = L.r_off + 2 * 16384;
     L.bar_off = L.raw_off + raw_stages * L.raw_stage;
     L.sf_off = L.r_off;
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
         }
         for (int s = 0; s < kTcMaxRawStages; ++s) {
             ptx::mbar_init(&raw_full[s], 1);
-            ptx::mbar_init(&raw_empty[s], kTcConvWarps);
+            ptx::mbar_init(&raw_empty[s], kTcConvWarps / 2);   // the warps of one half tile
         }
         ptx::mbar_init(d1_full, 1);
         ptx::mbar_init(d1_empty, kTcEpiWarps);
@@ -442,18 +443,19 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                         tc::tma_load_2d(xs + s * L.x_stage + a * 16384, &tmap, a * 64, row0, &x_full[s]);
                 }
             } else {
-                // E4M3 rows into the raw ring, each one chunk wider than the row
-                // (the extra chunk is outside the tensor: zero fill)
-                const unsigned bytes = (unsigned)(kTcRows * raw_row);
-                for (int i = 0; i < nt; ++i) {
-                    const int s = i % RS;
-                    const int use = i / RS;
+                // E4M3 half tiles (64 rows) into the raw ring, each row one chunk
+                // wider than stored (the extra chunk is outside the tensor: zero fill)
+                const unsigned bytes = (unsigned)(kTcRawRows * raw_row);
+                for (int u = 0; u < 2 * nt; ++u) {
+                    const int s = u % RS;
+                    const int use = u / RS;
                     if (use > 0 && !ptx::mbar_wait_bounded(&raw_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
                         atomicOr(p.status, kDevTimeout);
                         s_abort = 1;
                         break;
                     }
-                    const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kTcRows);
+                    const int row0 = (int)((int64_t)(b + (int64_t)(u >> 1) * grid) * kTcRows) +
+                                     (u & 1) * kTcRawRows;
                     ptx::mbar_arrive_expect_tx(&raw_full[s], bytes);
                     tc::tma_load_2d(raw + s * L.raw_stage, &tmap, 0, row0, &raw_full[s]);
                 }
@@ -509,49 +511,48 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
         }
     } else if (FP8 && warp >= 2 + kTcEpiWarps) {
         // ---- E4M3 -> FP16 converters ----------------------------------------------------
-        // thread ct takes tile rows ct, ct + 64: reads 16-byte chunks of its raw
-        // row (odd chunk stride: 8 consecutive rows hit distinct bank groups) and
-        // writes two 16-byte FP16 chunks into the 128B-swizzled operand tile
+        // thread ct takes tile row ct (warps 0-1 the first half tile, 2-3 the
+        // second): reads 16-byte chunks of its staged row (odd chunk stride:
+        // 8 consecutive rows hit distinct bank groups) and writes two 16-byte
+        // FP16 chunks per E4M3 chunk into the 128B-swizzled operand tile
         const int ct = (warp - 2 - kTcEpiWarps) * 32 + lane;
+        const int half = ct / kTcRawRows;
+        const int r = ct;
+        const uint32_t rx = (uint32_t)(r & 7);
         bool ok = true;
         for (int i = 0; i < nt; ++i) {
-            const int rs = i % RS;
+            const int u = 2 * i + half;
+            const int rs = u % RS;
             const int s = i % stages;
-            ok = ptx::mbar_wait_bounded(&raw_full[rs], (unsigned)(i / RS) & 1u, kSpinLimit);
+            ok = ptx::mbar_wait_bounded(&raw_full[rs], (unsigned)(u / RS) & 1u, kSpinLimit);
             if (ok && i >= stages)
                 ok = ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(i / stages - 1) & 1u, kSpinLimit);
             if (!ok)
                 break;
-            const uint8_t *src_t = raw + rs * L.raw_stage;
-            uint8_t *dst_t = xs + s * L.x_stage;
+            const uint8_t *src = raw + rs * L.raw_stage + (r - half * kTcRawRows) * raw_row;
+            uint8_t *dst_r = xs + s * L.x_stage + r * 128;
             // eight 16-byte loads in flight before converting (PA * 4 chunks
             // per row, a multiple of 4: the tail group is guarded)
-            for (int h = 0; h < kTcRows / (32 * kTcConvWarps); ++h) {
-                const int r = ct + h * 32 * kTcConvWarps;
-                const uint8_t *src = src_t + r * raw_row;
-                uint8_t *dst_r = dst_t + r * 128;
-                const uint32_t rx = (uint32_t)(r & 7);
-                for (int c0 = 0; c0 < PA * 4; c0 += 8) {
-                    uint4 a[8];
+            for (int c0 = 0; c0 < PA * 4; c0 += 8) {
+                uint4 a[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (c0 + u < PA * 4)
-                            a[u] = *reinterpret_cast<const uint4 *>(src + (c0 + u) * 16);
+                for (int v = 0; v < 8; ++v)
+                    if (c0 + v < PA * 4)
+                        a[v] = *reinterpret_cast<const uint4 *>(src + (c0 + v) * 16);
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int c = c0 + u;
-                        if (c < PA * 4) {
-                            uint4 o0, o1;
-                            tc::e4m3x4_to_f16(a[u].x, o0.x, o0.y);
-                            tc::e4m3x4_to_f16(a[u].y, o0.z, o0.w);
-                            tc::e4m3x4_to_f16(a[u].z, o1.x, o1.y);
-                            tc::e4m3x4_to_f16(a[u].w, o1.z, o1.w);
-                            // FP16 columns 16c .. 16c + 15: atom c / 4, chunks 2 (c % 4) and +1
-                            uint8_t *atom = dst_r + (c >> 2) * 16384;
-                            const uint32_t ch = (uint32_t)((c & 3) * 2);
-                            *reinterpret_cast<uint4 *>(atom + ((ch ^ rx) << 4)) = o0;
-                            *reinterpret_cast<uint4 *>(atom + (((ch + 1) ^ rx) << 4)) = o1;
-                        }
+                for (int v = 0; v < 8; ++v) {
+                    const int c = c0 + v;
+                    if (c < PA * 4) {
+                        uint4 o0, o1;
+                        tc::e4m3x4_to_f16(a[v].x, o0.x, o0.y);
+                        tc::e4m3x4_to_f16(a[v].y, o0.z, o0.w);
+                        tc::e4m3x4_to_f16(a[v].z, o1.x, o1.y);
+                        tc::e4m3x4_to_f16(a[v].w, o1.z, o1.w);
+                        // FP16 columns 16c .. 16c + 15: atom c / 4, chunks 2 (c % 4) and +1
+                        uint8_t *atom = dst_r + (c >> 2) * 16384;
+                        const uint32_t ch = (uint32_t)((c & 3) * 2);
+                        *reinterpret_cast<uint4 *>(atom + ((ch ^ rx) << 4)) = o0;
+                        *reinterpret_cast<uint4 *>(atom + (((ch + 1) ^ rx) << 4)) = o1;
                     }
                 }
             }
@@ -805,11 +806,11 @@ bool tc_supported(const glm_ctx *h)
 }
 
 // Ring depths that fit: operand-tile stages (2..4) and, for FP8 storage,
-// staged E4M3 tiles (2, else 1). Returns false if not even two operand stages fit.
+// staged E4M3 half tiles (3, else 2). Returns false if nothing fits.
 static bool tc_stages(int PA, bool fp8, int *stages, int *raw_stages)
 {
     for (int st = kTcMaxStages; st >= 2; --st) {
-        for (int rs = fp8 ? kTcMaxRawStages : 0; rs >= (fp8 ? 1 : 0); --rs) {
+        for (int rs = fp8 ? kTcMaxRawStages : 0; rs >= (fp8 ? 2 : 0); --rs) {
             if (tc_layout(PA, st, rs).total <= kSmemDynamicBudget) {
                 *stages = st;
                 *raw_stages = rs;
@@ -837,7 +838,7 @@ static glm_status_t tc_tensor_map(glm_ctx *h, const void *X)
         const int PA = (h->d.p + 63) / 64;
         const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld / 2, (cuuint64_t)h->d.n_rows};
         const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld};
-        const cuuint32_t box[2] = {(cuuint32_t)(PA * 32 + 8), (cuuint32_t)kTcRows};
+        const cuuint32_t box[2] = {(cuuint32_t)(PA * 32 + 8), (cuuint32_t)kTcRawRows};
         r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(X), dims, strides, box,
                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
