@@ -89,6 +89,15 @@ typedef struct {
 /* Never route K > 1 evaluations to the tensor-core kernel. */
 #define GLM_FLAG_NO_TENSOR_CORES 0x1u
 
+/* f and g without the prior terms: the likelihood sums over this handle's
+ * rows only. For row shards of one dataset evaluated separately (on several
+ * GPUs, or in pieces) and summed afterwards; one shard keeps the prior so it
+ * is counted once (§4.2.2 combine; the prior as in glm_logpost_grad). Applies
+ * to glm_logpost_grad and glm_logpost_grad_host; glm_rwm_run refuses such a
+ * handle (its accept step needs the whole posterior) and grouped calls always
+ * include the group prior. */
+#define GLM_FLAG_NO_PRIOR 0x2u
+
 /* Read-only facts about a handle (for reports and tuning). */
 typedef struct {
     int32_t sm_count;         /* SMs of the device                            */

@@ -29,6 +29,7 @@ GLM_X_BF16 = 1
 GLM_X_FP8E4M3 = 2
 
 GLM_FLAG_NO_TENSOR_CORES = 0x1
+GLM_FLAG_NO_PRIOR = 0x2
 
 ELEM_BYTES = {GLM_X_F32: 4, GLM_X_BF16: 2, GLM_X_FP8E4M3: 1}
 

@@ -215,8 +215,9 @@ static FusedParams base_params(const glm_ctx *h, const void *X, const float *x_s
     p.srow = h->srow;
     p.box_rows = h->box_rows;
     const double s2 = h->d.prior_sigma * h->d.prior_sigma;
-    p.inv_s2 = 1.0 / s2;
-    p.prior_const = 0.5 * (double)h->d.p * std::log(2.0 * M_PI * s2);
+    const bool prior = !(h->d.flags & GLM_FLAG_NO_PRIOR);
+    p.inv_s2 = prior ? 1.0 / s2 : 0.0;
+    p.prior_const = prior ? 0.5 * (double)h->d.p * std::log(2.0 * M_PI * s2) : 0.0;
     p.acc = h->acc;
     p.acc_flag = h->acc_flag;
     p.ticket = h->ticket;
@@ -349,7 +350,8 @@ glm_status_t glm_create(const glm_desc_t *desc, glm_handle_t *out)
     const glm_desc_t d = *desc;
     const int es = elem_bytes_of(d.xtype);
     if (es == 0 || d.n_rows < 0 || d.p < 1 || d.ld < d.p || d.k_max < 1 || d.k_max > 1024 ||
-        !(d.prior_sigma > 0.0) || !std::isfinite(d.prior_sigma) || d.device < 0)
+        !(d.prior_sigma > 0.0) || !std::isfinite(d.prior_sigma) || d.device < 0 ||
+        (d.flags & ~(GLM_FLAG_NO_TENSOR_CORES | GLM_FLAG_NO_PRIOR)) != 0)
         return GLM_ERR_INVALID_ARG;
     if (((int64_t)d.ld * es) % 16 != 0 || d.g_max < 0)
         return GLM_ERR_INVALID_ARG;
@@ -522,8 +524,8 @@ glm_status_t glm_rwm_run(glm_handle_t h, const void *X, const float *x_scale, co
                          const double *log_u, float *beta_state, double *f_state, int32_t init_f,
                          float *samples, uint8_t *accept, double *logpost, glm_stream_t stream)
 {
-    if (!h)
-        return GLM_ERR_INVALID_ARG;
+    if (!h || (h->d.flags & GLM_FLAG_NO_PRIOR))
+        return GLM_ERR_INVALID_ARG;     // the accept step needs the whole posterior
     glm_status_t st = check_x_args(h, X, x_scale, y);
     if (st != GLM_OK)
         return st;

@@ -874,6 +874,7 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
     const int PA = (P + 63) / 64;
     const int MB = (P + 127) / 128;
     const double s2 = h->d.prior_sigma * h->d.prior_sigma;
+    const bool prior = !(h->d.flags & GLM_FLAG_NO_PRIOR);
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(h->tc_map);
     const bool fp8 = h->d.xtype == GLM_X_FP8E4M3;
     int stages = 0, raw_stages = 0;
@@ -924,8 +925,8 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         rc.numAttrs = 1;
         if (cudaLaunchKernelEx(&rc, tc_reduce_kernel, (const double *)h->tc_part_f,
                                (const float *)h->tc_part_g, h->sm_count, KB, MB * 128, P, kk, ng,
-                               beta + (size_t)k0 * P, x_scale, 1.0 / s2,
-                               0.5 * (double)P * std::log(2.0 * M_PI * s2), f_out + k0,
+                               beta + (size_t)k0 * P, x_scale, prior ? 1.0 / s2 : 0.0,
+                               prior ? 0.5 * (double)P * std::log(2.0 * M_PI * s2) : 0.0, f_out + k0,
                                g_out + (size_t)k0 * P) != cudaSuccess)
             return GLM_ERR_CUDA;
     }
