@@ -58,11 +58,15 @@ PROFILE_MD = os.path.join(ROOT, "profiles", "fused_f32_big.md")
 KERNEL_SOURCES = ["paper_1310_1537_gb300/csrc/glm_fused.cuh",
                   "paper_1310_1537_gb300/csrc/glm_fused_f32.cu",
                   "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
+TC_SOURCES = ["paper_1310_1537_gb300/csrc/glm_tc.cu",
+              "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
+GROUPED_SOURCES = ["paper_1310_1537_gb300/csrc/glm_grouped.cu",
+                   "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in (sources or KERNEL_SOURCES):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -88,16 +92,16 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
+def profile_traffic(md=PROFILE_MD, sources=None):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
     on the current kernel source (else None)."""
     try:
-        text = open(PROFILE_MD).read()
+        text = open(md).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_tr or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_tr or m_hash.group(1) != kernel_source_hash(sources):
         return None
     return float(m_tr.group(1))
 
@@ -487,7 +491,11 @@ def run_batched(args, local, fp8=False):
                            "CUDA-core fused pass, chunks of 8 vectors",
                    "l2": f"inputs larger than L2 (X {n * p * es / 1e6:.0f} MB), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": profile_traffic(os.path.join(
+                         ROOT, "profiles", "tc_fp8_batched.md" if fp8 else "tc_bf16_batched.md"),
+                         TC_SOURCES) if tc else None,
+                     "traffic_source": "ncu dram bytes of the tensor-core kernel, one launch",
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": bytes_step, "kernel_ms": step_ms,
                      "kernel_ms_def": "whole call (all launches of one step)",
@@ -589,7 +597,10 @@ def run_grouped(args, local):
                    "step": "one CUDA-graph replay of the autotuned grouped launch",
                    "l2": f"X {n * p * 4 / 1e6:.0f} MB vs 129 MB L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": profile_traffic(os.path.join(ROOT, "profiles", "grouped_hb.md"),
+                                                GROUPED_SOURCES),
+                     "traffic_source": "ncu dram bytes of the grouped kernel, one launch",
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": bytes_step, "kernel_ms": step_ms},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
