@@ -27,8 +27,9 @@
 // in FP16 range and is divided out of eta exactly.
 //
 // Warp roles: warp 0 issues TMA loads, warp 1 allocates tensor memory and one
-// of its threads issues the MMAs, warps 2..17 run the epilogue (and first load
-// beta into tensor memory), warps 18..19 convert FP8 tiles (FP8 storage only).
+// of its threads issues the MMAs, warps 2..17 first load beta into tensor
+// memory and then run the epilogue, and with FP8 storage warps 18..21
+// convert the staged tiles.
 // Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -373,7 +374,9 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
     // (part 1) term of beta_k, two columns of beta per 32-bit cell. FP8
     // storage: the coefficients are s_j beta_kj times 2^e_k, with e_k the
     // power of two that brings max_j |s_j beta_kj| just under 2^14.
-    if (warp >= 2 && warp < 6) {
+    constexpr int EPI0 = 2;                         // first epilogue warp
+    constexpr int CONV0 = 2 + kTcEpiWarps;          // first converter warp (FP8)
+    if (warp >= EPI0 && warp < EPI0 + 4) {
         const int q = warp & 3;
         const int n = q * 32 + lane;
         const int k = n >> 1;
@@ -423,8 +426,8 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
     __syncthreads();
     tc::fence_after();
     ptx::grid_dep_launch_dependents();
-
-    if (warp == 0) {
+    if (warp < 2) {
+      if (warp == 0) {
         // ---- TMA producer ------------------------------------------------------------
         if (lane == 0) {
             if constexpr (!FP8) {
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                 }
             }
         }
-    } else if (warp == 1) {
+      } else if (warp == 1) {
         // ---- MMA issuer ----------------------------------------------------------------
         if (lane == 0) {
             const uint32_t xs_a = ptx::smem_u32(xs);
@@ -509,13 +512,14 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
             if (nt > 0)
                 tc::commit(d2_done);
         }
-    } else if (FP8 && warp >= 2 + kTcEpiWarps) {
+      }
+    } else if (FP8 && warp >= CONV0) {
         // ---- E4M3 -> FP16 converters ----------------------------------------------------
         // thread ct takes tile row ct (warps 0-1 the first half tile, 2-3 the
         // second): reads 16-byte chunks of its staged row (odd chunk stride:
         // 8 consecutive rows hit distinct bank groups) and writes two 16-byte
         // FP16 chunks per E4M3 chunk into the 128B-swizzled operand tile
-        const int ct = (warp - 2 - kTcEpiWarps) * 32 + lane;
+        const int ct = (warp - CONV0) * 32 + lane;
         const int half = ct / kTcRawRows;
         const int r = ct;
         const uint32_t rx = (uint32_t)(r & 7);
@@ -572,7 +576,7 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
         constexpr int CW = kTcEpiCols;
         constexpr int RT = kTcEpiRows;
         const int q = warp & 3;                 // tensor-memory lane quarter
-        const int hh = (warp - 2) >> 2;         // tile rows CW*hh .. CW*hh + CW - 1
+        const int hh = (warp - EPI0) >> 2;      // tile rows CW*hh .. CW*hh + CW - 1
         const int n = q * 32 + lane;            // D1 lane
         const int k = n >> 1;                   // vector
         const int part = n & 1;                 // 0: beta_hi lane, 1: beta_lo lane
@@ -708,7 +712,7 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
         if (part == 0)
             sf[hh * 64 + k] = fv;
         asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
-        const int et = tid - 64;
+        const int et = tid - 32 * EPI0;
         if (et < p.kk) {
             double tot = 0.0;
             for (int g2 = 0; g2 < kTcEpiGroups; ++g2)

@@ -196,11 +196,33 @@ def test_grouped_autotuner_keeps_results_correct():
 
 @pytest.mark.parametrize("narrow", ["0", "1"])
 def test_grouped_both_kernel_variants(narrow, monkeypatch):
+    """The warp-stream kernel and the narrow-row kernel (forced through the
+    environment) on ragged, empty and single-row groups and several row
+    widths."""
     monkeypatch.setenv("GLM_GROUPED_NARROW", narrow)
     sizes = np.array([20, 0, 1, 57, 3000, 33, 0, 512, 31, 32, 64, 1, 2, 4000, 777])
-    for p in (8, 32):
+    for p in (8, 32, 100):
         gd = synth.make_grouped(len(sizes), p, 3 + p, dtype=np.float32, sizes=sizes)
-        (f, g), = _run_grouped(gd.X, gd.y, gd.offsets, gd.beta, gd.mu, gd.tau, p)
-        f_o, g_o = _oracle_grouped(gd.X.astype(np.float64), gd.y, gd.offsets,
+        ld = synth.padded_ld(p, 4)
+        Xs = synth.pad_columns(gd.X, ld)
+        (f, g), = _run_grouped(Xs, gd.y, gd.offsets, gd.beta, gd.mu, gd.tau, p)
+        f_o, g_o = _oracle_grouped(Xs.astype(np.float64), gd.y, gd.offsets,
                                    gd.beta.astype(np.float32), gd.mu.astype(np.float32), gd.tau, p)
         assert_close(f, g, f_o, g_o, what=f"variant narrow={narrow} P={p}")
+
+
+def test_grouped_many_tiny_groups_among_long_ones():
+    """Hundreds of 0-3 row groups mixed with long groups (many group
+    switches inside one 32-row slot), deterministic, at P=32 and P=100."""
+    rng = np.random.default_rng(91)
+    sizes = np.concatenate([rng.integers(0, 4, 700), [9000], rng.integers(0, 3, 500), [20000]])
+    for p in (32, 100):
+        gd = synth.make_grouped(len(sizes), p, 93 + p, dtype=np.float32, sizes=sizes)
+        ld = synth.padded_ld(p, 4)
+        Xs = synth.pad_columns(gd.X, ld)
+        outs = _run_grouped(Xs, gd.y, gd.offsets, gd.beta, gd.mu, gd.tau, p, repeat=2)
+        np.testing.assert_array_equal(outs[0][0], outs[1][0])
+        np.testing.assert_array_equal(outs[0][1], outs[1][1])
+        f_o, g_o = _oracle_grouped(Xs.astype(np.float64), gd.y, gd.offsets,
+                                   gd.beta.astype(np.float32), gd.mu.astype(np.float32), gd.tau, p)
+        assert_close(outs[0][0], outs[0][1], f_o, g_o, what=f"crowded P={p}")
