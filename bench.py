@@ -8,7 +8,7 @@ over X, accept in FP64 — one kernel launch. The metric is log-posterior +
 gradient evaluations per second (one per step), whole job over all ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload big|batched|batched-fp8|grouped|serving]
+                    [--workload big|small|batched|batched-fp8|grouped|serving]
 
 ``--impl reference`` times the FP64 CPU oracle on this machine's host cores
 (the same workload, a bounded row sample per step when a full evaluation
@@ -17,6 +17,10 @@ would not fit the time budget). Rank 0 prints one JSON line.
 The default workload is the one above. The others measure the remaining
 parts of the path, each printing its own JSON line:
 
+- ``small``: N = 10,000, P = 50 (FP64 data stored FP32, ld 52), K = 1: 100
+  evaluation points, then Metropolis steps (one launch each). X fits in L2,
+  so the line reports steps/s and µs per step (launch/latency-bound) with no
+  HBM fraction.
 - ``batched`` / ``batched-fp8``: N = 1,000,000, P = 256, K = 64 vectors per
   call, X BF16 (tensor-core pass) or FP8 E4M3 with column scales; one step is
   one call evaluating all 64 vectors. Also times the FP32 path on the same
@@ -24,7 +28,7 @@ parts of the path, each printing its own JSON line:
 - ``grouped``: 4,000 hierarchical-Bayes groups (log-normal sizes, median
   400, about 2.5M rows), P = 32, X FP32; one step is one replay of a CUDA
   graph holding the autotuned grouped launch (all groups' f and g).
-- ``serving``: Poisson arrivals at 2,000 requests/s against 16 resident BF16
+- ``serving``: Poisson arrivals at 2,000 requests/s (``--rate``; 0 submits all at once) against 16 resident BF16
   datasets (N log-uniform in [1e3, 4e6], P log-uniform in [8, 512]), K
   uniform in 1..32 per request; one step is one request. Reports latency
   percentiles from submission to results on the host.
@@ -614,6 +618,87 @@ def run_grouped(args, local):
     glm.glm_destroy(h)
 
 
+def run_small(args, local):
+    import torch
+    import synth
+    import paper_1310_1537_gb300 as glm
+    n, p = 10_000, 50
+    torch.cuda.set_device(local)
+    seed = synth.seed_for(0)
+    d = synth.make_glm(n, p, seed, dtype=np.float64)
+    ld = synth.padded_ld(p, 4)
+    X32 = synth.pad_columns(d.X.astype(np.float32), ld)
+    Xd = torch.from_numpy(X32).cuda()
+    yd = torch.from_numpy(d.y).cuda()
+    h = glm.glm_create(n, p, ld, 8, glm.GLM_X_F32, PRIOR_SIGMA, local, 0)
+    # 100 evaluation points, 8 per call
+    pts = synth.eval_points(d.beta_star, 100, 0.1, seed + 1).astype(np.float32)
+    Pd = torch.from_numpy(pts).cuda()
+    f = torch.empty(8, dtype=torch.float64, device="cuda")
+    g = torch.empty((8, p), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for i in range(0, 100, 8):
+        kk = min(8, 100 - i)
+        glm.glm_logpost_grad(h, Xd, None, yd, Pd[i:i + kk], kk, f, g, stream)
+    steps, warmup = args.steps, args.warmup
+    z, lu = synth.rwm_streams(steps + warmup, 1, p, seed + 3)
+    zd = torch.from_numpy(z).cuda()
+    lud = torch.from_numpy(lu).cuda()
+    step = synth.rwm_step_size(n, p)
+    state = torch.from_numpy(d.beta_star[None, :].astype(np.float32)).cuda()
+    fst = torch.zeros(1, dtype=torch.float64, device="cuda")
+    samples = torch.empty((steps + warmup, 1, p), dtype=torch.float32, device="cuda")
+    acc = torch.empty((steps + warmup, 1), dtype=torch.uint8, device="cuda")
+    lp = torch.empty((steps + warmup, 1), dtype=torch.float64, device="cuda")
+    glm.glm_rwm_run(h, Xd, None, yd, 1, warmup, step, zd, lud, state, fst, 1, samples, acc, lp,
+                    stream)
+    assert glm.glm_sync(h, stream) == glm.GLM_OK
+    sampler = _gpu_sampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    glm.glm_rwm_run(h, Xd, None, yd, 1, steps, step, zd[warmup:], lud[warmup:], state, fst, 0,
+                    samples[warmup:], acc[warmup:], lp[warmup:], stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    assert glm.glm_sync(h, stream) == glm.GLM_OK
+    total_ms = ev0.elapsed_time(ev1)
+    # end to end: host-buffer evaluations (beta in, f and g out, synchronised)
+    bh = torch.from_numpy(d.beta_star[None, :].astype(np.float32)).pin_memory()
+    fh = torch.empty(1, dtype=torch.float64).pin_memory()
+    gh = torch.empty((1, p), dtype=torch.float32).pin_memory()
+    for _ in range(5):
+        glm.glm_logpost_grad_host(h, Xd, None, yd, bh, 1, fh, gh, stream)
+    e2e_n = max(100, min(steps, 2000))
+    t0 = time.perf_counter()
+    for _ in range(e2e_n):
+        glm.glm_logpost_grad_host(h, Xd, None, yd, bh, 1, fh, gh, stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_n
+    cpu_v, cpu_sample = _oracle_rate(d.X, d.y, d.beta_star, p, 5.0, n)
+    acc_rate = float(acc[warmup:].float().mean().item())
+    _emit({
+        "metric": "Metropolis steps/s (one log-posterior+grad eval each)",
+        "value": steps / (total_ms / 1e3), "unit": "steps/s", "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"small: N={n}, P={p} (ld {ld}), X FP32 from FP64 data, K=1, "
+                               "100 evaluation points then Metropolis steps",
+                   "l2": "X 2.1 MB: L2-resident, no flush; latency/launch-bound",
+                   "acceptance_rate": acc_rate},
+        "roofline": None,
+        "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": cpu_sample},
+        "e2e": {"value": 1.0 / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": p * 4,
+                "d2h_bytes_per_step": 8 + p * 4,
+                "api": "glm_logpost_grad_host (beta in, f and g out, synchronised)"},
+        "clocks": clocks, "gpu_launches": steps,
+    })
+    glm.glm_destroy(h)
+
+
 SERVING_RATE = 2000.0
 
 
@@ -650,7 +735,9 @@ def run_serving(args, local):
         it = dsets[i]
         b = (it["d"].beta_star[None, :] + 0.05 * rng.standard_normal((k, it["p"])))
         reqs.append((i, k, np.ascontiguousarray(b, dtype=np.float32)))
-    arrivals = synth.poisson_arrivals(SERVING_RATE, count, seed + 101)
+    rate = SERVING_RATE if args.rate is None else args.rate
+    arrivals = (synth.poisson_arrivals(rate, count, seed + 101) if rate > 0
+                else np.zeros(count))
     rids = [0] * count
     submit_lag = np.zeros(count)
     ready = threading.Semaphore(0)
@@ -733,9 +820,10 @@ def run_serving(args, local):
         "warmup": args.warmup, "ms_per_step": span_s * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"serving: Poisson {SERVING_RATE:.0f} requests/s, 16 resident "
-                               "BF16 datasets (N log-uniform [1e3, 4e6], P log-uniform "
-                               "[8, 512]), K uniform 1..32 per request",
+        "config": {"workload": (f"serving: Poisson {rate:.0f} requests/s" if rate > 0 else
+                                "serving: all requests submitted at once (saturation)") +
+                               ", 16 resident BF16 datasets (N log-uniform [1e3, 4e6], "
+                               "P log-uniform [8, 512]), K uniform 1..32 per request",
                    "step": "one request", "streams": 4, "max_batch_k": 64,
                    "datasets": [[it["n"], it["p"]] for it in dsets],
                    "l2": "datasets 0.79 GB in total, mostly larger than L2; no flush"},
@@ -777,8 +865,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rate", type=float, default=None,
+                    help="serving arrival rate in requests/s (0: all at once); default 2000")
     ap.add_argument("--workload", default="big",
-                    choices=["big", "batched", "batched-fp8", "grouped", "serving"])
+                    choices=["big", "small", "batched", "batched-fp8", "grouped", "serving"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -791,7 +881,8 @@ def main():
                               "the oracle arm is timed for the default workload only; the "
                               "other workload lines carry their own cpu_baseline"}))
             return
-        {"batched": lambda: run_batched(args, local),
+        {"small": lambda: run_small(args, local),
+         "batched": lambda: run_batched(args, local),
          "batched-fp8": lambda: run_batched(args, local, fp8=True),
          "grouped": lambda: run_grouped(args, local),
          "serving": lambda: run_serving(args, local)}[args.workload]()
