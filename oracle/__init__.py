@@ -263,3 +263,108 @@ def dequantize_e4m3(Q, scale, p=None):
     P = len(scale) if p is None else int(p)
     v = e4m3_decode(Q[:, :P])
     return v * np.asarray(scale, dtype=np.float64)[None, :P]
+
+
+# ---------------------------------------------------------------------------
+# Univariate slice sampling (Neal 2003: stepping out, then shrinkage) inside
+# Gibbs sweeps over the coefficients, §3.4.4. The oracle evaluates every
+# point with the plain definition of the log-posterior (logpost_grad); it
+# does not use the differential update.
+#
+# Interval arithmetic is FP32 with each operation rounded separately (the
+# coefficients are FP32 state): L0 = x0 - w*U, R0 = L0 + w,
+# L_j = L0 - j*w, R_j = R0 + j*w, x1 = L + U*(R - L); J = floor(m*V) and
+# K = m - 1 - J. The slice level is log y = g(x0) + log_u0 (FP64). After
+# s_max rejected shrinkage proposals the coordinate keeps x0.
+
+def slice_step(logdens, x0, g0, log_u0, uni, w, m, s_max):
+    """One univariate slice-sampling update of a scalar.
+
+    logdens(x: float32) -> float64 log density; x0 float32 with
+    g0 = logdens(x0); uni = [U, V, shrink_0, ..., shrink_{s_max-1}] float32.
+    Returns (x1, g1, n_shrink, n_evals, moved).
+    """
+    f32 = np.float32
+    x0 = f32(x0)
+    w = f32(w)
+    log_y = float(g0) + float(log_u0)
+    U, V = f32(uni[0]), f32(uni[1])
+    L0 = f32(x0 - f32(w * U))
+    R0 = f32(L0 + w)
+    J = int(np.floor(f32(f32(m) * V)))
+    K = (m - 1) - J
+    evals = 0
+    L = L0
+    j = 0
+    while J > 0:
+        Lj = f32(L0 - f32(f32(j) * w))
+        evals += 1
+        if not log_y < logdens(Lj):
+            L = Lj
+            break
+        j += 1
+        J -= 1
+        L = f32(L0 - f32(f32(j) * w))
+    R = R0
+    j = 0
+    while K > 0:
+        Rj = f32(R0 + f32(f32(j) * w))
+        evals += 1
+        if not log_y < logdens(Rj):
+            R = Rj
+            break
+        j += 1
+        K -= 1
+        R = f32(R0 + f32(f32(j) * w))
+    for t in range(s_max):
+        x1 = f32(L + f32(f32(uni[2 + t]) * f32(R - L)))
+        g1 = logdens(x1)
+        evals += 1
+        if log_y < g1:
+            return x1, g1, t, evals, True
+        if x1 < x0:
+            L = x1
+        else:
+            R = x1
+    return x0, float(g0), s_max, evals, False
+
+
+def slice_gibbs(X, y, beta0, log_u0, uni, w, m, prior_sigma=10.0, p=None):
+    """Gibbs sweeps of univariate slice sampling over beta (float32 state).
+
+    log_u0 (S, P), uni (S, P, 2 + s_max) from synth.slice_streams.
+    Returns dict(xk (S,P) f32: coordinate value after each update,
+    gk (S,P) f64: log-posterior after each update, nshrink (S,P),
+    evals (S,P), beta (P,) f32 final, f final, f0 initial).
+    """
+    Xd = _f64_matrix(X)
+    P = Xd.shape[1] if p is None else int(p)
+    beta = np.array(beta0, dtype=np.float32).reshape(P)
+    S = log_u0.shape[0]
+    s_max = uni.shape[2] - 2
+
+    def f_of(b):
+        f, _ = logpost_grad(Xd, y, b.astype(np.float64), prior_sigma=prior_sigma, p=P)
+        return float(f[0])
+
+    g = f_of(beta)
+    f0 = g
+    xk = np.empty((S, P), dtype=np.float32)
+    gk = np.empty((S, P), dtype=np.float64)
+    nsh = np.empty((S, P), dtype=np.int32)
+    nev = np.empty((S, P), dtype=np.int32)
+    for s in range(S):
+        for k in range(P):
+            def dens(x, k=k):
+                b = beta.copy()
+                b[k] = x
+                return f_of(b)
+            x1, g1, ns, ne, _ = slice_step(dens, beta[k], g, log_u0[s, k], uni[s, k], w, m,
+                                           s_max)
+            beta[k] = x1
+            g = g1
+            xk[s, k] = x1
+            gk[s, k] = g1
+            nsh[s, k] = ns
+            nev[s, k] = ne
+    return {"xk": xk, "gk": gk, "nshrink": nsh, "evals": nev, "beta": beta, "f": g, "f0": f0}

@@ -128,6 +128,23 @@ def rwm_streams(n_steps: int, k: int, p: int, seed: int):
     return z, np.log(u)
 
 
+def slice_streams(n_sweeps: int, p: int, s_max: int, seed: int):
+    """Random numbers of Gibbs sweeps with univariate slice sampling.
+
+    log_u0 (n_sweeps, P) float64: log of the uniform that sets each slice
+    level; uni (n_sweeps, P, 2 + s_max) float32: per coordinate update the
+    interval-placement uniform, the stepping-out split uniform and s_max
+    shrinkage uniforms, all in (0, 1). Both the oracle and the device read
+    these buffers.
+    """
+    rng = np.random.default_rng(seed)
+    u0 = rng.random((n_sweeps, p))
+    u0 = np.where(u0 > 0.0, u0, 0.5)
+    uni = rng.random((n_sweeps, p, 2 + s_max)).astype(np.float32)
+    uni = np.where(uni > 0.0, uni, np.float32(0.5)).astype(np.float32)
+    return np.log(u0), uni
+
+
 def rwm_step_size(n: int, p: int) -> float:
     """Proposal scale 2.38/sqrt(P) * 1/sqrt(N/4) (Laplace-scale guess)."""
     return 2.38 / math.sqrt(p) / math.sqrt(max(n, 1) / 4.0)
