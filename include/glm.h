@@ -398,6 +398,73 @@ GLM_API glm_status_t glm_server_stats(glm_server_t s, glm_server_stats_t *stats)
  * (not the datasets' memory). Requests still waiting are dropped. */
 GLM_API glm_status_t glm_server_destroy(glm_server_t s);
 
+/* ------------------------------------------------------------------------
+ * Gibbs sweeps of univariate slice sampling with the differential update of
+ * X beta (§3.4.4). The sampler updates one coefficient at a time; changing
+ * beta_k by d changes eta = X beta by d X_k, so with eta kept on the device a
+ * log-posterior evaluation along coordinate k reads column k of X only.
+ * X is stored column-major here ("Xt": column k at Xt + k * ld, FP32).
+ *
+ * Each coordinate update is Neal's slice sampler: slice level
+ * log y = f(beta) + log u0; initial interval L0 = x0 - w U, R0 = L0 + w;
+ * stepping out at most J = floor(m V) steps left and K = m - 1 - J right
+ * (L_j = L0 - j w, R_j = R0 + j w); then shrinkage proposals
+ * x1 = L + S_t (R - L) until log y < f(x1), moving the interval end on the
+ * side of x1 toward x1 otherwise. Interval arithmetic is FP32 with each
+ * operation rounded separately. After s_max rejected proposals the
+ * coordinate keeps x0. f is the full log-posterior (likelihood plus the
+ * N(0, s^2 I) prior, as for glm_logpost_grad). Random numbers are inputs:
+ * log_u0 (n_sweeps x P FP64) and uni (n_sweeps x P x (2 + s_max) FP32: U, V,
+ * then the shrinkage uniforms S_t), all uniforms in (0, 1).
+ * ---------------------------------------------------------------------- */
+typedef struct glm_slice *glm_slice_t;
+
+typedef struct {
+    int64_t n_rows;       /* N >= 1                                            */
+    int64_t ld;           /* column stride of Xt in elements: >= N, multiple of 4 */
+    int32_t p;            /* P >= 1                                            */
+    int32_t m;            /* stepping-out limit, 1..16                         */
+    int32_t s_max;        /* shrinkage proposals per update, 1..64             */
+    int32_t device;
+    float w;              /* initial interval width > 0                        */
+    double prior_sigma;   /* s > 0                                             */
+} glm_slice_desc_t;
+
+/* Create a sampler for one dataset shape. GLM_ERR_UNSUPPORTED when a CTA's
+ * rows (about N / 152) do not fit in shared memory (N above about 2.5 M). */
+GLM_API glm_status_t glm_slice_create(const glm_slice_desc_t *desc, glm_slice_t *out);
+GLM_API glm_status_t glm_slice_destroy(glm_slice_t s);
+
+/* eta = X beta (device N FP32) from Xt and beta (device P FP32). Needed
+ * before the first glm_slice_run of a chain and whenever beta is set by the
+ * caller. */
+GLM_API glm_status_t glm_slice_eta(glm_slice_t s, const float *Xt, const float *beta, float *eta,
+                                   glm_stream_t stream);
+
+/* The log-posterior at beta with beta_k replaced by x[c], c < M <= 16
+ * (device FP32 candidates), into f_out[c] (device FP64): one pass over column
+ * k and eta, which must equal X beta. */
+GLM_API glm_status_t glm_slice_coord_logpost(glm_slice_t s, const float *Xt, const uint8_t *y,
+                                             const float *eta, const float *beta, int32_t k,
+                                             const float *x, int32_t M, double *f_out,
+                                             glm_stream_t stream);
+
+/* n_sweeps Gibbs sweeps (coordinates 0..P-1 in order) from the state
+ * (beta, eta = X beta, f_state = f(beta); init_f = 1 computes f_state first),
+ * one cooperative launch. Updates beta, eta and f_state in place (device).
+ * Optional per-update outputs (device, n_sweeps x P, or NULL): xk_out the
+ * coordinate's new value, gk_out f after the update, nshrink_out rejected
+ * shrinkage proposals (s_max: kept x0). Asynchronous; a bounded device wait
+ * that expires is reported by glm_slice_sync as GLM_ERR_TIMEOUT (the state
+ * is then not valid). */
+GLM_API glm_status_t glm_slice_run(glm_slice_t s, const float *Xt, const uint8_t *y, float *eta,
+                                   float *beta, double *f_state, int32_t init_f, int32_t n_sweeps,
+                                   const double *log_u0, const float *uni, float *xk_out,
+                                   double *gk_out, int32_t *nshrink_out, glm_stream_t stream);
+
+/* Synchronise the stream and return the sampler's device status. */
+GLM_API glm_status_t glm_slice_sync(glm_slice_t s, glm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,8 @@ EXPORTS = (
     "glm_sync", "glm_selftest_wait_timeout", "glm_logpost_grad_noalloc",
     "glm_autotune_grouped", "glm_server_create", "glm_server_add_dataset", "glm_server_submit",
     "glm_server_poll", "glm_server_wait", "glm_server_stats", "glm_server_destroy",
+    "glm_slice_create", "glm_slice_destroy", "glm_slice_eta", "glm_slice_coord_logpost",
+    "glm_slice_run", "glm_slice_sync",
 )
 
 
@@ -78,6 +80,12 @@ class glm_server_stats_t(C.Structure):
                 ("vectors_done", C.c_int64), ("hbm_budget_bytes", C.c_int64),
                 ("hbm_in_flight_bytes", C.c_int64), ("max_concurrent_batches", C.c_int32),
                 ("last_cuda_error", C.c_int32), ("last_error_site", C.c_int32)]
+
+
+class glm_slice_desc_t(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("ld", C.c_int64), ("p", C.c_int32), ("m", C.c_int32),
+                ("s_max", C.c_int32), ("device", C.c_int32), ("w", C.c_float),
+                ("prior_sigma", C.c_double)]
 
 
 _lib = None
@@ -125,6 +133,14 @@ def load(build_if_missing: bool = True):
                                  C.c_int32], st),
             "glm_server_stats": ([vp, C.POINTER(glm_server_stats_t)], st),
             "glm_server_destroy": ([vp], st),
+            "glm_slice_create": ([C.POINTER(glm_slice_desc_t), C.POINTER(vp)], st),
+            "glm_slice_destroy": ([vp], st),
+            "glm_slice_eta": ([vp, vp, vp, vp, vp], st),
+            "glm_slice_coord_logpost": ([vp, vp, vp, vp, vp, C.c_int32, vp, C.c_int32, vp, vp],
+                                        st),
+            "glm_slice_run": ([vp, vp, vp, vp, vp, vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp,
+                               vp], st),
+            "glm_slice_sync": ([vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -302,3 +318,39 @@ def glm_server_stats(s) -> dict:
 
 def glm_server_destroy(s) -> None:
     _check(load().glm_server_destroy(s), "glm_server_destroy")
+
+
+def glm_slice_create(n_rows, p, ld, w=1.0, m=4, s_max=30, prior_sigma=10.0, device=0):
+    """Gibbs-slice sampler for column-major X (N rows, column stride ld)."""
+    d = glm_slice_desc_t(int(n_rows), int(ld), int(p), int(m), int(s_max), int(device),
+                         float(w), float(prior_sigma))
+    s = C.c_void_p()
+    _check(load().glm_slice_create(C.byref(d), C.byref(s)), "glm_slice_create")
+    return s.value
+
+
+def glm_slice_destroy(s) -> None:
+    _check(load().glm_slice_destroy(s), "glm_slice_destroy")
+
+
+def glm_slice_eta(s, Xt, beta, eta, stream=None) -> None:
+    _check(load().glm_slice_eta(s, _ptr(Xt), _ptr(beta), _ptr(eta), _stream(stream)),
+           "glm_slice_eta")
+
+
+def glm_slice_coord_logpost(s, Xt, y, eta, beta, k, x, M, f_out, stream=None) -> None:
+    _check(load().glm_slice_coord_logpost(s, _ptr(Xt), _ptr(y), _ptr(eta), _ptr(beta), int(k),
+                                          _ptr(x), int(M), _ptr(f_out), _stream(stream)),
+           "glm_slice_coord_logpost")
+
+
+def glm_slice_run(s, Xt, y, eta, beta, f_state, init_f, n_sweeps, log_u0, uni, xk_out=None,
+                  gk_out=None, nshrink_out=None, stream=None) -> None:
+    _check(load().glm_slice_run(s, _ptr(Xt), _ptr(y), _ptr(eta), _ptr(beta), _ptr(f_state),
+                                int(init_f), int(n_sweeps), _ptr(log_u0), _ptr(uni),
+                                _ptr(xk_out), _ptr(gk_out), _ptr(nshrink_out), _stream(stream)),
+           "glm_slice_run")
+
+
+def glm_slice_sync(s, stream=None) -> int:
+    return int(load().glm_slice_sync(s, _stream(stream)))
