@@ -8,7 +8,7 @@ over X, accept in FP64 — one kernel launch. The metric is log-posterior +
 gradient evaluations per second (one per step), whole job over all ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload big|small|batched|batched-fp8|grouped|serving]
+                    [--workload big|small|batched|batched-fp8|grouped|serving|slice]
 
 ``--impl reference`` times the FP64 CPU oracle on this machine's host cores
 (the same workload, a bounded row sample per step when a full evaluation
@@ -28,6 +28,10 @@ parts of the path, each printing its own JSON line:
 - ``grouped``: 4,000 hierarchical-Bayes groups (log-normal sizes, median
   400, about 2.5M rows), P = 32, X FP32; one step is one replay of a CUDA
   graph holding the autotuned grouped launch (all groups' f and g).
+- ``slice``: Gibbs sweeps of univariate slice sampling with the
+  differential update of X beta (column-major X, N = 2,000,000, P = 100,
+  FP32, w = 4.5/sqrt(N), m = 4); one step is one sweep (P coordinate
+  updates, each several evaluation passes over one column).
 - ``serving``: Poisson arrivals at 2,000 requests/s (``--rate``; 0 submits all at once) against 16 resident BF16
   datasets (N log-uniform in [1e3, 4e6], P log-uniform in [8, 512]), K
   uniform in 1..32 per request; one step is one request. Reports latency
@@ -66,6 +70,8 @@ TC_SOURCES = ["paper_1310_1537_gb300/csrc/glm_tc.cu",
               "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 GROUPED_SOURCES = ["paper_1310_1537_gb300/csrc/glm_grouped.cu",
                    "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
+SLICE_SOURCES = ["paper_1310_1537_gb300/csrc/glm_slice.cu",
+                 "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 
 
 def kernel_source_hash(sources=None) -> str:
@@ -104,7 +110,7 @@ def profile_traffic(md=PROFILE_MD, sources=None):
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_(?:launch|update):\s*([0-9.eE+]+)", text)
     if not m_hash or not m_tr or m_hash.group(1) != kernel_source_hash(sources):
         return None
     return float(m_tr.group(1))
@@ -699,6 +705,124 @@ def run_small(args, local):
     glm.glm_destroy(h)
 
 
+def run_slice(args, local):
+    import torch
+    import synth
+    import paper_1310_1537_gb300 as glm
+    n, p = N_ROWS, P
+    torch.cuda.set_device(local)
+    seed = synth.seed_for(1)
+    d = make_data()
+    ld = (n + 3) // 4 * 4
+    Xt = torch.from_numpy(np.ascontiguousarray(d.X.T)).cuda()      # P x N column-major X
+    y = torch.from_numpy(d.y).cuda()
+    w, m, s_max = 4.5 / math.sqrt(n), 4, 30
+    spec = args.spec if args.spec > 0 else 2
+    sm = glm.glm_slice_create(n, p, ld, w=w, m=m, s_max=s_max, spec=spec)
+    sweeps, warm = args.steps, args.warmup
+    lu, uni = synth.slice_streams(warm + sweeps, p, s_max, seed + 9)
+    lud, unid = torch.from_numpy(lu).cuda(), torch.from_numpy(uni).cuda()
+    beta = torch.from_numpy(d.beta_star.astype(np.float32)).cuda()
+    eta = torch.empty(n, dtype=torch.float32, device="cuda")
+    fs = torch.zeros(1, dtype=torch.float64, device="cuda")
+    xk = torch.empty((warm + sweeps, p), dtype=torch.float32, device="cuda")
+    gk = torch.empty((warm + sweeps, p), dtype=torch.float64, device="cuda")
+    ns = torch.empty((warm + sweeps, p), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    glm.glm_slice_eta(sm, Xt, beta, eta, stream)
+    glm.glm_slice_run(sm, Xt, y, eta, beta, fs, 1, warm, lud, unid, xk, gk, ns, stream)
+    assert glm.glm_slice_sync(sm, stream) == glm.GLM_OK
+    sampler = _gpu_sampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    glm.glm_slice_run(sm, Xt, y, eta, beta, fs, 0, sweeps, lud[warm:], unid[warm:], xk[warm:],
+                      gk[warm:], ns[warm:], stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    assert glm.glm_slice_sync(sm, stream) == glm.GLM_OK
+    total_ms = ev0.elapsed_time(ev1)
+    updates = sweeps * p
+    nsh = ns[warm:].cpu().numpy()
+    # evaluation passes: one stepping-out pass (when J + K > 0; m > 1 here) plus
+    # the shrinkage passes, spec proposals each, up to the accepted proposal
+    props = np.minimum(nsh + 1, s_max)
+    passes = int(updates + ((props + spec - 1) // spec).sum())
+    # end to end: each sweep's random numbers in from pinned host memory and its
+    # per-update results out, one run per sweep
+    luh = torch.from_numpy(lu[warm:]).pin_memory()
+    unh = torch.from_numpy(uni[warm:]).pin_memory()
+    xh = torch.empty((sweeps, p), dtype=torch.float32).pin_memory()
+    gh = torch.empty((sweeps, p), dtype=torch.float64).pin_memory()
+    lub = torch.empty((1, p), dtype=torch.float64, device="cuda")
+    unb = torch.empty((1, p, 2 + s_max), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(sweeps):
+        lub.copy_(luh[i:i + 1], non_blocking=True)
+        unb.copy_(unh[i:i + 1], non_blocking=True)
+        glm.glm_slice_run(sm, Xt, y, eta, beta, fs, 0, 1, lub, unb, xk[i:i + 1], gk[i:i + 1],
+                          None, stream)
+        xh[i].copy_(xk[i], non_blocking=True)
+        gh[i].copy_(gk[i], non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    assert glm.glm_slice_sync(sm, stream) == glm.GLM_OK
+    # the oracle: plain log-posterior evaluations (no differential update) on a
+    # row prefix, scaled to N rows and to this run's evaluations per update
+    import oracle
+    oracle.build()
+    rows = 200_000
+    X64 = d.X[:rows].astype(np.float64)
+    b64 = d.beta_star.astype(np.float64)
+    reps, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < 8.0 or reps < 2:
+        oracle.logpost_grad(X64, d.y[:rows], b64)
+        reps += 1
+    eval_s = (time.perf_counter() - t1) / reps * n / rows
+    # the oracle evaluates each stepping-out point separately (J + K = m - 1)
+    oracle_evals = (m - 1) + props.sum() / updates
+    cpu_v = 1.0 / (oracle_evals * eval_s)
+    peak, peak_kind = measured_hbm_peak()
+    bytes_update = n * 4 + p * 4 * 2
+    achieved = bytes_update * updates / (total_ms / 1e3) / 1e9
+    _emit({
+        "metric": "slice-sampler coordinate updates/s", "value": updates / (total_ms / 1e3),
+        "unit": "updates/s", "n_gpus": 1, "steps": sweeps, "warmup": warm,
+        "ms_per_step": total_ms / sweeps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Gibbs slice sampling with differential update: N={n}, P={p}, "
+                               f"X FP32 column-major, w={w:.3g}, m={m}, s_max={s_max}, "
+                               f"spec={spec}",
+                   "step": "one sweep: P coordinate updates in one cooperative launch",
+                   "passes_per_update": passes / updates,
+                   "us_per_pass": total_ms * 1e3 / passes,
+                   "l2": "each update reads one 8 MB column from HBM; eta and y stay in "
+                         "shared memory"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak,
+                     "traffic": profile_traffic(os.path.join(ROOT, "profiles", "slice_run_big.md"),
+                                                SLICE_SOURCES),
+                     "traffic_unit": "DRAM bytes per coordinate update",
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_update": bytes_update,
+                     "note": "each update is several evaluation passes joined by grid "
+                             "barriers: latency-bound, not bandwidth-bound"},
+        "cpu_baseline": {"value": cpu_v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{reps} plain evaluations on rows [0, {rows}), scaled to "
+                                   f"N={n} and {oracle_evals:.2f} evaluations per update"},
+        "e2e": {"value": updates / e2e_s, "unit": "updates/s",
+                "h2d_bytes_per_step": p * (8 + 4 * (2 + s_max)), "d2h_bytes_per_step": p * 12,
+                "api": "glm_slice_run per sweep with its random numbers copied in and "
+                       "per-update results copied out"},
+        "clocks": clocks, "gpu_launches": 1,
+    })
+    glm.glm_slice_destroy(sm)
+
+
 SERVING_RATE = 2000.0
 
 
@@ -867,8 +991,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rate", type=float, default=None,
                     help="serving arrival rate in requests/s (0: all at once); default 2000")
+    ap.add_argument("--spec", type=int, default=0,
+                    help="slice workload: shrinkage proposals per evaluation pass (0: 2)")
     ap.add_argument("--workload", default="big",
-                    choices=["big", "small", "batched", "batched-fp8", "grouped", "serving"])
+                    choices=["big", "small", "batched", "batched-fp8", "grouped", "serving",
+                             "slice"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -882,6 +1009,7 @@ def main():
                               "other workload lines carry their own cpu_baseline"}))
             return
         {"small": lambda: run_small(args, local),
+         "slice": lambda: run_slice(args, local),
          "batched": lambda: run_batched(args, local),
          "batched-fp8": lambda: run_batched(args, local, fp8=True),
          "grouped": lambda: run_grouped(args, local),

@@ -412,7 +412,11 @@ GLM_API glm_status_t glm_server_destroy(glm_server_t s);
  * x1 = L + S_t (R - L) until log y < f(x1), moving the interval end on the
  * side of x1 toward x1 otherwise. Interval arithmetic is FP32 with each
  * operation rounded separately. After s_max rejected proposals the
- * coordinate keeps x0. f is the full log-posterior (likelihood plus the
+ * coordinate keeps x0. The device evaluates the next `spec` proposals of
+ * the shrinkage sequence in one pass (each assuming the earlier ones are
+ * rejected, as the sequence is fixed by the random numbers until the first
+ * acceptance) and applies them in order: the result equals one proposal at a
+ * time. f is the full log-posterior (likelihood plus the
  * N(0, s^2 I) prior, as for glm_logpost_grad). Random numbers are inputs:
  * log_u0 (n_sweeps x P FP64) and uni (n_sweeps x P x (2 + s_max) FP32: U, V,
  * then the shrinkage uniforms S_t), all uniforms in (0, 1).
@@ -427,6 +431,8 @@ typedef struct {
     int32_t s_max;        /* shrinkage proposals per update, 1..64             */
     int32_t device;
     float w;              /* initial interval width > 0                        */
+    int32_t spec;         /* shrinkage proposals per evaluation pass, 1..16;
+                             0 selects the default (2)                        */
     double prior_sigma;   /* s > 0                                             */
 } glm_slice_desc_t;
 

@@ -85,7 +85,7 @@ class glm_server_stats_t(C.Structure):
 class glm_slice_desc_t(C.Structure):
     _fields_ = [("n_rows", C.c_int64), ("ld", C.c_int64), ("p", C.c_int32), ("m", C.c_int32),
                 ("s_max", C.c_int32), ("device", C.c_int32), ("w", C.c_float),
-                ("prior_sigma", C.c_double)]
+                ("spec", C.c_int32), ("prior_sigma", C.c_double)]
 
 
 _lib = None
@@ -320,10 +320,11 @@ def glm_server_destroy(s) -> None:
     _check(load().glm_server_destroy(s), "glm_server_destroy")
 
 
-def glm_slice_create(n_rows, p, ld, w=1.0, m=4, s_max=30, prior_sigma=10.0, device=0):
-    """Gibbs-slice sampler for column-major X (N rows, column stride ld)."""
+def glm_slice_create(n_rows, p, ld, w=1.0, m=4, s_max=30, prior_sigma=10.0, device=0, spec=0):
+    """Gibbs-slice sampler for column-major X (N rows, column stride ld);
+    spec = shrinkage proposals per evaluation pass (0: default)."""
     d = glm_slice_desc_t(int(n_rows), int(ld), int(p), int(m), int(s_max), int(device),
-                         float(w), float(prior_sigma))
+                         float(w), int(spec), float(prior_sigma))
     s = C.c_void_p()
     _check(load().glm_slice_create(C.byref(d), C.byref(s)), "glm_slice_create")
     return s.value

@@ -40,11 +40,13 @@ struct glm_slice {
 
 namespace glm {
 
-constexpr int kSliceThreads = 256;
+constexpr int kSliceThreads = 512;
 constexpr int kSliceMaxCand = 16;          // candidates per evaluation pass
 constexpr int kSliceMaxShrink = 64;
 constexpr int kSliceEvalBlocks = 1024;     // standalone evaluation grid
+constexpr int kSliceSpecDefault = 2;       // shrinkage proposals per pass
 constexpr unsigned kGridSpinLimit = 1u << 22;
+static_assert(kSliceMaxShrink + 2 <= kSliceThreads, "one random number per thread");
 
 struct SliceParams {
     const float *Xt;           // column-major, column k at Xt + k * ld
@@ -59,6 +61,7 @@ struct SliceParams {
     int n_sweeps;
     int m;
     int s_max;
+    int spec;
     float w;
     double inv_s2;
     double prior_const;
@@ -117,13 +120,40 @@ __host__ __device__ inline SliceLayout slice_layout(int rows_max, int P, int s_m
     L.y_off = o;
     o += (rows_max + 15) / 16 * 16;
     L.misc_off = o;
-    // misc: beta (P floats), warp sums (8 x 16 floats), candidates (16 floats),
+    // misc: beta (P floats), warp sums (warps x 16 floats), candidates (16 floats),
     // g values (16 doubles), stream buffers 2 x (2 + s_max) floats + 2 doubles,
     // control words, two mbarriers
-    o += ((P * 4 + 15) / 16) * 16 + 8 * kSliceMaxCand * 4 + kSliceMaxCand * 4 +
+    o += ((P * 4 + 15) / 16) * 16 + (kSliceThreads / 32) * kSliceMaxCand * 4 + kSliceMaxCand * 4 +
          kSliceMaxCand * 8 + 2 * (((2 + s_max) * 4 + 15) / 16 * 16 + 16) + 256 + 64;
     L.total = o + 128;
     return L;
+}
+
+// Candidates per evaluation pass rounded up to a compiled size.
+__device__ __forceinline__ int slice_mc(int M)
+{
+    return M <= 4 ? M : M <= 8 ? 8 : 16;
+}
+
+// This thread's sums of ell(eta_i + d[c] x_i) over rows i = tid, tid + NT, ...
+// for the MC candidate shifts d[0..MC) (MC a compile-time size: candidates
+// beyond M are padding and their sums are not used). Few candidates leave
+// little work per row, so those loops are unrolled over rows to keep several
+// rows' loads and exp/log in flight.
+template <int MC, int U>
+__device__ __forceinline__ void slice_rows(const float *xb, const float *etas, const uint8_t *ys,
+                                           int R, const float *d, float *acc)
+{
+#pragma unroll
+    for (int c = 0; c < MC; ++c)
+        acc[c] = 0.0f;
+#pragma unroll U
+    for (int i = threadIdx.x; i < R; i += kSliceThreads) {
+        const float x = xb[i], e = etas[i], yv = (float)ys[i];
+#pragma unroll
+        for (int c = 0; c < MC; ++c)
+            acc[c] += sl::ell(fmaf(d[c], x, e), yv);
+    }
 }
 
 __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams p)
@@ -141,8 +171,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
     uint8_t *misc = smem + L.misc_off;
     float *bs = reinterpret_cast<float *>(misc);                        // beta
     int o = ((p.P * 4 + 15) / 16) * 16;
-    float *wsum = reinterpret_cast<float *>(misc + o);                  // [8][16]
-    o += 8 * kSliceMaxCand * 4;
+    float *wsum = reinterpret_cast<float *>(misc + o);                  // [warps][16]
+    o += (NT / 32) * kSliceMaxCand * 4;
     float *cand = reinterpret_cast<float *>(misc + o);                  // [16] candidate values
     o += kSliceMaxCand * 4;
     double *gval = reinterpret_cast<double *>(misc + o);                // [16]
@@ -210,25 +240,29 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
     auto eval_pass = [&](int M, const float *xb, double S2_wo_k, float x0) -> bool {
         float acc[kSliceMaxCand], dl[kSliceMaxCand];
 #pragma unroll
-        for (int c = 0; c < kSliceMaxCand; ++c) {
-            acc[c] = 0.0f;
+        for (int c = 0; c < kSliceMaxCand; ++c)
             dl[c] = c < M ? __fsub_rn(cand[c], x0) : 0.0f;
-        }
-        for (int i = tid; i < R; i += NT) {
-            const float x = xb[i], e = etas[i], yv = (float)ys[i];
-#pragma unroll
-            for (int c = 0; c < kSliceMaxCand; ++c)
-                if (c < M)
-                    acc[c] += sl::ell(fmaf(dl[c], x, e), yv);
-        }
+        const int MP = slice_mc(M);
+        if (MP == 1)
+            slice_rows<1, 4>(xb, etas, ys, R, dl, acc);
+        else if (MP == 2)
+            slice_rows<2, 4>(xb, etas, ys, R, dl, acc);
+        else if (MP == 3)
+            slice_rows<3, 2>(xb, etas, ys, R, dl, acc);
+        else if (MP == 4)
+            slice_rows<4, 2>(xb, etas, ys, R, dl, acc);
+        else if (MP == 8)
+            slice_rows<8, 1>(xb, etas, ys, R, dl, acc);
+        else
+            slice_rows<16, 1>(xb, etas, ys, R, dl, acc);
 #pragma unroll
         for (int c = 0; c < kSliceMaxCand; ++c) {
-            if (c < M) {
+            if (c < MP) {
                 float v = acc[c];
 #pragma unroll
                 for (int mm = 16; mm > 0; mm >>= 1)
                     v += __shfl_xor_sync(FULL, v, mm);
-                if (lane == 0)
+                if (lane == 0 && c < M)
                     wsum[warp * kSliceMaxCand + c] = v;
             }
         }
@@ -268,12 +302,19 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
         ++pass;
         if (!ctl[0])
             return false;
-        if (tid < M) {
+        // warp c sums the CTAs' partials of candidate c: lane-strided sums,
+        // then a shuffle tree (the same fixed order in every CTA)
+        for (int c = warp; c < M; c += NT / 32) {
             double v = 0.0;
-            for (int q = 0; q < G; ++q)
-                v += __ldcg(part + (size_t)q * kSliceMaxCand + tid);
-            const double x = (double)cand[tid];
-            gval[tid] = v - 0.5 * p.inv_s2 * (S2_wo_k + x * x) - p.prior_const;
+            for (int q = lane; q < G; q += 32)
+                v += __ldcg(part + (size_t)q * kSliceMaxCand + c);
+#pragma unroll
+            for (int mm = 16; mm > 0; mm >>= 1)
+                v += __shfl_xor_sync(FULL, v, mm);
+            if (lane == 0) {
+                const double x = (double)cand[c];
+                gval[c] = v - 0.5 * p.inv_s2 * (S2_wo_k + x * x) - p.prior_const;
+            }
         }
         __syncthreads();
         return true;
@@ -324,8 +365,16 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
                 issue_col(u + 1);
             inflight[buf ^ 1] = true;
         }
-        if (u + 1 < n_up)
-            load_stream(u + 1);
+        // the next update's random numbers: loaded into registers now, stored
+        // to shared memory after this update's passes (latency hidden)
+        double nxt_lu = 0.0;
+        float nxt_un = 0.0f;
+        if (u + 1 < n_up) {
+            if (tid == 0)
+                nxt_lu = __ldg(p.log_u0 + u + 1);
+            if (tid < 2 + p.s_max)
+                nxt_un = __ldg(p.uni + (int64_t)(u + 1) * (2 + p.s_max) + tid);
+        }
         const float *xb = xs + buf * p.rows_max;
         const uint8_t *sbuf = stream_buf + buf * sb;
         const double log_u0 = *reinterpret_cast<const double *>(sbuf);
@@ -368,28 +417,49 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
                     break;
             Rf = __fadd_rn(R0, __fmul_rn((float)kk, w));
         }
-        // shrinkage
+        // shrinkage, spec proposals per pass: proposal q of a pass assumes
+        // proposals 0..q-1 rejected (each rejection only moves the interval
+        // end on its own side), so the first accepted one in order is the
+        // sequential result
         float x1 = x0;
         double g1 = g0;
         int nsh = p.s_max;
-        for (int t = 0; t < p.s_max && alive; ++t) {
-            const float xc = __fadd_rn(Lf, __fmul_rn(un[2 + t], __fsub_rn(Rf, Lf)));
-            if (tid == 0)
-                cand[0] = xc;
+        for (int t = 0; t < p.s_max && alive;) {
+            const int D = min(p.spec, p.s_max - t);
+            __syncthreads();                  // the previous pass's cand[] is read
+            if (tid == 0) {
+                float Lc = Lf, Rc = Rf;
+                for (int q = 0; q < D; ++q) {
+                    const float xc = __fadd_rn(Lc, __fmul_rn(un[2 + t + q], __fsub_rn(Rc, Lc)));
+                    cand[q] = xc;
+                    if (xc < x0)
+                        Lc = xc;
+                    else
+                        Rc = xc;
+                }
+            }
             __syncthreads();
-            alive = eval_pass(1, xb, S2k, x0);
+            alive = eval_pass(D, xb, S2k, x0);
             if (!alive)
                 break;
-            if (log_y < gval[0]) {
-                x1 = xc;
-                g1 = gval[0];
-                nsh = t;
-                break;
+            bool acc_ok = false;
+            for (int q = 0; q < D; ++q) {
+                const float xc = cand[q];
+                if (log_y < gval[q]) {
+                    x1 = xc;
+                    g1 = gval[q];
+                    nsh = t + q;
+                    acc_ok = true;
+                    break;
+                }
+                if (xc < x0)
+                    Lf = xc;
+                else
+                    Rf = xc;
             }
-            if (xc < x0)
-                Lf = xc;
-            else
-                Rf = xc;
+            if (acc_ok)
+                break;
+            t += D;
         }
         if (!alive)
             break;
@@ -398,6 +468,13 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
         if (dlt != 0.0f)
             for (int i = tid; i < R; i += NT)
                 etas[i] = fmaf(dlt, xb[i], etas[i]);
+        if (u + 1 < n_up) {
+            uint8_t *dst = stream_buf + (buf ^ 1) * sb;
+            if (tid == 0)
+                *reinterpret_cast<double *>(dst) = nxt_lu;
+            if (tid < 2 + p.s_max)
+                reinterpret_cast<float *>(dst + 16)[tid] = nxt_un;
+        }
         __syncthreads();
         if (tid == 0) {
             bs[k] = x1;
@@ -523,7 +600,7 @@ glm_status_t glm_slice_create(const glm_slice_desc_t *desc, glm_slice_t *out)
     if (d.n_rows < 1 || d.p < 1 || d.ld < d.n_rows || d.ld % 4 != 0 || d.m < 1 ||
         d.m > kSliceMaxCand || d.s_max < 1 || d.s_max > kSliceMaxShrink || !(d.w > 0.0f) ||
         !std::isfinite(d.w) || !(d.prior_sigma > 0.0) || !std::isfinite(d.prior_sigma) ||
-        d.device < 0)
+        d.device < 0 || d.spec < 0 || d.spec > kSliceMaxCand)
         return GLM_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -659,6 +736,7 @@ glm_status_t glm_slice_run(glm_slice_t s, const float *Xt, const uint8_t *y, flo
     p.n_sweeps = n_sweeps;
     p.m = s->d.m;
     p.s_max = s->d.s_max;
+    p.spec = s->d.spec > 0 ? s->d.spec : kSliceSpecDefault;
     p.w = s->d.w;
     const double s2 = s->d.prior_sigma * s->d.prior_sigma;
     p.inv_s2 = 1.0 / s2;

@@ -117,14 +117,15 @@ def test_slice_sampler_rejects_bad_descriptors_without_a_device():
     lib = pkg.load()
     s = C.c_void_p()
     assert lib.glm_slice_create(None, C.byref(s)) == pkg.GLM_ERR_INVALID_ARG
-    good = dict(n_rows=1000, ld=1000, p=5, m=4, s_max=30, device=0, w=1.0, prior_sigma=10.0)
+    good = dict(n_rows=1000, ld=1000, p=5, m=4, s_max=30, device=0, w=1.0, spec=0,
+                prior_sigma=10.0)
     bad = [dict(n_rows=0), dict(ld=999), dict(ld=1002), dict(p=0), dict(m=0), dict(m=17),
            dict(s_max=0), dict(s_max=65), dict(w=0.0), dict(w=float("inf")),
-           dict(prior_sigma=0.0), dict(device=-1)]
+           dict(prior_sigma=0.0), dict(device=-1), dict(spec=-1), dict(spec=17)]
     for b in bad:
         d = dict(good, **b)
         desc = pkg.glm_slice_desc_t(d["n_rows"], d["ld"], d["p"], d["m"], d["s_max"],
-                                    d["device"], d["w"], d["prior_sigma"])
+                                    d["device"], d["w"], d["spec"], d["prior_sigma"])
         assert lib.glm_slice_create(C.byref(desc), C.byref(s)) == pkg.GLM_ERR_INVALID_ARG, b
         assert s.value is None
     assert lib.glm_slice_run(None, None, None, None, None, None, 0, 0, None, None, None, None,

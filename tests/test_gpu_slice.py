@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 class Chain:
     """Device copies of one column-major dataset and a sampler for it."""
 
-    def __init__(self, n, p, seed, w=0.5, m=4, s_max=30):
+    def __init__(self, n, p, seed, w=0.5, m=4, s_max=30, spec=0):
         d = synth.make_glm(n, p, seed, dtype=np.float32)
         self.d, self.n, self.p = d, n, p
         self.ld = (n + 3) // 4 * 4
@@ -35,7 +35,7 @@ class Chain:
         self.Xt = to_dev(Xt)
         self.y = to_dev(d.y)
         self.w, self.m, self.s_max = w, m, s_max
-        self.s = glm.glm_slice_create(n, p, self.ld, w=w, m=m, s_max=s_max)
+        self.s = glm.glm_slice_create(n, p, self.ld, w=w, m=m, s_max=s_max, spec=spec)
 
     def close(self):
         glm.glm_slice_destroy(self.s)
@@ -166,6 +166,27 @@ def test_slice_run_is_deterministic_and_resumable():
         np.testing.assert_array_equal(second[3], a[3])
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("m", [1, 4, 9])
+def test_speculative_shrinkage_equals_one_proposal_per_pass(m):
+    """Evaluating several shrinkage proposals per pass is exact: every spec
+    gives bitwise the same chain as spec = 1 (one proposal per pass), with
+    wide intervals (many shrinkage steps) and s_max small enough to be hit."""
+    n, p, sweeps, s_max = 7001, 5, 4, 6
+    lu, uni = synth.slice_streams(sweeps, p, s_max, 950 + m)
+    out = {}
+    for spec in (1, 2, 3, 7, 16):
+        c = Chain(n, p, 951, w=2.0, m=m, s_max=s_max, spec=spec)
+        try:
+            r = c.run(c.d.beta_star.astype(np.float32), lu, uni)
+            out[spec] = r[:5] + (r[5].cpu().numpy(),)
+        finally:
+            c.close()
+    for spec in (2, 3, 7, 16):
+        for a, b in zip(out[1], out[spec]):
+            np.testing.assert_array_equal(a, b)
+    assert (out[1][2] == s_max).any() or out[1][2].max() >= 3
 
 
 def test_slice_full_size_big_workload():
