@@ -86,6 +86,11 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
 // log-likelihood term y t - softplus(t), overflow-free, fast exp/log
 __device__ __forceinline__ float ell(float t, float yv)
 {
@@ -277,13 +282,15 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
         // grid barrier: arrivals counted, bounded wait, abort flag
         __syncthreads();
         if (tid == 0) {
-            __threadfence();
-            atomicAdd(p.counter, 1u);
+            // release: the partials written before the block barrier are
+            // visible to any CTA whose acquire load sees this arrival
+            sl::red_add_release(p.counter, 1u);
             const unsigned target = (pass + 1u) * (unsigned)G;
             unsigned it = 0;
             int ok = 1;
             while (sl::ld_acquire(p.counter) < target) {
-                if (sl::ld_acquire(p.abort_flag) != 0u) {
+                // the abort flag is polled every 64th round: one load per round
+                if ((it & 63u) == 63u && sl::ld_acquire(p.abort_flag) != 0u) {
                     ok = 0;
                     break;
                 }
@@ -293,10 +300,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1) slice_run_kernel(SliceParams
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
-            __threadfence();
-            ctl[0] = ok;
+            ctl[0] = ok;                          // the acquire load above orders the reads below
         }
         __syncthreads();
         ++pass;

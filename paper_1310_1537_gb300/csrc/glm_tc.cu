@@ -467,8 +467,14 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
       } else if (warp == 1) {
         // ---- MMA issuer ----------------------------------------------------------------
         if (lane == 0) {
-            const uint32_t xs_a = ptx::smem_u32(xs);
-            const uint32_t rb_a = ptx::smem_u32(rb);
+            // descriptors are built once and stepped by adding the address
+            // offset / 16 (the low 14-bit field; shared addresses stay below
+            // 256 KB, so no carry): one thread issues every MMA, and its
+            // per-MMA work bounds the issue rate
+            const uint64_t bk0 = tc::mdesc(ptx::smem_u32(xs), 16, 1024);       // X, K-major
+            const uint64_t am0 = tc::mdesc(ptx::smem_u32(xs), 16384, 1024);    // X, MN-major
+            const uint64_t rm0 = tc::mdesc(ptx::smem_u32(rb), 16384, 1024);    // R, MN-major
+            const uint64_t stage_step = (uint64_t)(L.x_stage >> 4);
             bool ok = true;
             for (int i = 0; i <= nt && ok; ++i) {
                 if (i < nt) {
@@ -479,10 +485,14 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                     if (!ok)
                         break;
                     tc::fence_after();
-                    const uint32_t xa = xs_a + s * L.x_stage;
-                    for (int ks = 0; ks < PA * 4; ++ks) {
-                        const uint64_t bd = tc::mdesc(xa + (ks >> 2) * 16384 + (ks & 3) * 32, 16, 1024);
-                        tc::mma_ta(tmem + kTcD1Col, tmem + kTcB1Col + ks * 8, bd, ID1, ks > 0 ? 1u : 0u);
+                    const uint64_t bks = bk0 + (uint64_t)s * stage_step;
+                    for (int a = 0; a < PA; ++a) {
+                        const uint64_t bda = bks + (uint64_t)(a * (16384 >> 4));
+                        const uint32_t aa = tmem + kTcB1Col + a * 32;
+#pragma unroll
+                        for (int sub = 0; sub < 4; ++sub)     // 16 columns: 32 bytes, 8 cells
+                            tc::mma_ta(tmem + kTcD1Col, aa + 8 * sub, bda + 2 * sub, ID1,
+                                       (a | sub) ? 1u : 0u);
                     }
                     tc::commit(d1_full);
                 }
@@ -493,13 +503,14 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                     if (!ok)
                         break;
                     tc::fence_after();
-                    const uint32_t xa = xs_a + sj * L.x_stage;
+                    const uint64_t ams = am0 + (uint64_t)sj * stage_step;
                     for (int mb = 0; mb < MB; ++mb) {
-                        for (int ks = 0; ks < kTcRows / 16; ++ks) {
-                            const uint64_t ad = tc::mdesc(xa + (2 * mb) * 16384 + ks * 16 * 128, 16384, 1024);
-                            const uint64_t bd = tc::mdesc(rb_a + ks * 16 * 128, 16384, 1024);
-                            tc::mma(tmem + kTcD2Col + mb * 128, ad, bd, ID2, (j > 0 || ks > 0) ? 1u : 0u);
-                        }
+                        const uint64_t adm = ams + (uint64_t)(2 * mb * (16384 >> 4));
+                        const uint32_t dt = tmem + kTcD2Col + mb * 128;
+#pragma unroll
+                        for (int ks = 0; ks < kTcRows / 16; ++ks)     // 16 rows = 2 KB each
+                            tc::mma(dt, adm + (uint64_t)(ks * 128), rm0 + (uint64_t)(ks * 128), ID2,
+                                    (j > 0 || ks > 0) ? 1u : 0u);
                     }
                     tc::commit(&x_empty[sj]);
                     tc::commit(r_empty);
