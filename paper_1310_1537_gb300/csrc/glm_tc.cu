@@ -208,15 +208,34 @@ __device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_
         "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-// TR map with the fast hardware exp/log/reciprocal; overflow-free forms.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// TR map on the hardware base-2 exponential and logarithm, overflow-free:
+// with e = exp(-|eta|) and L = log2(1 + e),
+//   ell = y eta - max(eta, 0) - L ln 2,
+//   sigma(eta) = exp(min(eta, 0)) / (1 + e) = 2^(min(eta, 0) log2(e) - L),
+// so the logistic needs one more exponential and no reciprocal or select.
 __device__ __forceinline__ void tr_fast(float eta, float yv, float &ell, float &r)
 {
-    const float e = __expf(-fabsf(eta));                  // exp(-|eta|) in (0, 1]
-    const float d = 1.0f + e;
-    ell = fmaf(yv, eta, -fmaxf(eta, 0.0f));               // y eta - max(eta, 0)
-    ell = fmaf(-0.69314718055994531f, __log2f(d), ell);   // - log(1 + exp(-|eta|))
-    const float inv = __fdividef(1.0f, d);
-    r = yv - (eta >= 0.0f ? inv : e * inv);
+    constexpr float kLog2e = 1.4426950408889634f;
+    constexpr float kLn2 = 0.69314718055994531f;
+    const float e = ex2_approx(-fabsf(eta) * kLog2e);     // exp(-|eta|) in (0, 1]
+    const float L = lg2_approx(1.0f + e);
+    ell = fmaf(yv, eta, -fmaxf(eta, 0.0f));
+    ell = fmaf(-kLn2, L, ell);
+    r = yv - ex2_approx(fmaf(fminf(eta, 0.0f), kLog2e, -L));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -593,6 +612,10 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
         const int part = n & 1;                 // 0: beta_hi lane, 1: beta_lo lane
         const bool active = k < p.kk;
         const int tb = CW * hh + RT * part;     // this thread's RT rows
+        // the lo lane walks its rows rotated by 4 (row (j + 4) mod 16 at step
+        // j): its R-tile stores then fall in other 16-byte chunks of the
+        // swizzle than the hi lane's, and the two halves do not conflict
+        const int rot = part ? 4 : 0;
         float vs = 1.0f;                        // 2^-e_k (FP8 storage)
         if constexpr (FP8)
             vs = vscale[k];
@@ -616,7 +639,18 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                         dst[j >> 2] |= (uint32_t)__ldg(p.y + r0 + j) << (8 * (j & 3));
             }
         };
+        // labels in the lo lane's row order: words rotated by one
+        auto rotate_y = [&](uint32_t *y4) {
+            if (part) {
+                const uint32_t t0 = y4[0];
+#pragma unroll
+                for (int w = 0; w < RT / 4 - 1; ++w)
+                    y4[w] = y4[w + 1];
+                y4[RT / 4 - 1] = t0;
+            }
+        };
         load_y(0, yw);
+        rotate_y(yw);
         bool ok = true;
         for (int i = 0; i < nt; ++i) {
             load_y(i + 1, yn);
@@ -641,8 +675,9 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
             float mine[RT];
 #pragma unroll
             for (int j = 0; j < RT; ++j) {
-                const float send = part ? v[j] : v[RT + j];
-                mine[j] = (part ? v[RT + j] : v[j]) + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
+                const int pj = (j + 4) & (RT - 1);
+                const float send = part ? v[j] : v[RT + pj];
+                mine[j] = (part ? v[RT + pj] : v[j]) + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
                 if constexpr (FP8)
                     mine[j] *= vs;
             }
@@ -663,7 +698,7 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                     const float yv = (float)((yw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
                     float ell, r;
                     tc::tr_fast(mine[j], yv, ell, r);
-                    const bool in = j < nvalid;
+                    const bool in = ((j + rot) & (RT - 1)) < nvalid;
                     facc += in ? ell : 0.0f;
                     r = in ? r : 0.0f;
                     float rh, rl;
@@ -677,11 +712,19 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
             }
             // R tile rows tb..tb+RT-1 (tb is a multiple of 8), columns 2k (hi)
             // and 2k+1 (lo): the 128B swizzle permutes 16-byte chunks by row & 7
-            uint8_t *rrow = rb + (k >> 5) * 16384 + tb * 128 + (((2 * k) & 7) << 1);
+            const uint32_t rrow = (uint32_t)((k >> 5) * 16384 + tb * 128 + (((2 * k) & 7) << 1));
             const uint32_t chunk = (uint32_t)((2 * k) & 63) >> 3;
+            // row (j + rot) mod 16: (j + 4) & 7 = (j & 7) ^ 4, so the lo lane
+            // uses the hi lane's addressing with its chunk flipped by 4 and
+            // its base moved by 4 rows (back 12 rows from step 12 on)
+            const uint32_t chk = chunk ^ (uint32_t)rot;
+            const uint32_t base_a = rrow + (uint32_t)(rot * 128);
+            const uint32_t base_b = base_a - (uint32_t)(rot * 512);
 #pragma unroll
-            for (int j = 0; j < RT; ++j)
-                *reinterpret_cast<uint32_t *>(rrow + j * 128 + ((chunk ^ (uint32_t)(j & 7)) << 4)) = w[j];
+            for (int j = 0; j < RT; ++j) {
+                const uint32_t bj = (j < RT - 4) ? base_a : base_b;
+                *reinterpret_cast<uint32_t *>(rb + (bj + j * 128 + ((chk ^ (uint32_t)(j & 7)) << 4))) = w[j];
+            }
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0)
@@ -689,6 +732,7 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
 #pragma unroll
             for (int t = 0; t < RT / 4; ++t)
                 yw[t] = yn[t];
+            rotate_y(yw);
         }
         if (!ok) {
             atomicOr(p.status, kDevTimeout);
