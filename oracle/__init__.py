@@ -19,6 +19,12 @@ Functions and the passages they follow:
   log-posterior (§2.2, §3.4.4); FP32 state, FP64 acceptance.
 * ``bf16_from_f32``, ``quantize_e4m3``, ``e4m3_value`` — reduced-precision
   storage of X (bfloat16 RNE; OCP E4M3 with power-of-two column scales).
+* ``slice_step``, ``slice_gibbs`` — Gibbs sweeps of univariate slice sampling
+  over the coefficients (§3.4.4), evaluated with the plain log-posterior.
+* ``ising_half_sweep``, ``ising_gibbs``, ``ising_energy``,
+  ``ising_to_plane``, ``ising_from_planes`` — checkerboard Gibbs sampling of
+  the square-lattice Ising model (§4.3.1) in the natural row-major layout
+  (NumPy, FP64); the colour planes only index the uniforms.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against closed
 forms, extended-precision brute force, finite differences, symmetries,
@@ -368,3 +374,90 @@ def slice_gibbs(X, y, beta0, log_u0, uni, w, m, prior_sigma=10.0, p=None):
             nsh[s, k] = ns
             nev[s, k] = ne
     return {"xk": xk, "gk": gk, "nshrink": nsh, "evals": nev, "beta": beta, "f": g, "f0": f0}
+
+
+# ---------------------------------------------------------------------------
+# Square-lattice Ising model, checkerboard Gibbs sampling (§4.3.1).
+#
+# Spins s_i in {0, 1} on an R x C lattice (C even), each interacting with its
+# 4 lattice neighbours; free boundary (a missing neighbour contributes
+# nothing). The Gibbs conditional is P(s_i = 1 | rest) = 1 / (1 + exp(-z_i)),
+# z_i = b_i + w * sum_j s_j over the neighbours j of i (the paper's
+# eq-ising-p); the energy consistent with it is
+# E(s) = -sum_i b_i s_i - w * sum_<ij> s_i s_j, P(s) proportional to exp(-E).
+# Colour c holds the sites with (row + col) % 2 == c; the two colours are
+# updated in turn, each site i of the colour set to 1 iff u_i < P(s_i = 1).
+# Colour plane c lists colour c's sites row by row: plane entry (r, j) is the
+# site (r, 2j + ((r + c) % 2)).
+
+
+def ising_to_plane(a, color):
+    """Colour plane `color` of a natural-layout R x C array: (R, C // 2)."""
+    a = np.asarray(a)
+    R, C = a.shape
+    out = np.empty((R, C // 2), dtype=a.dtype)
+    for r in range(R):
+        start = (r + color) % 2
+        out[r] = a[r, start::2]
+    return out
+
+
+def ising_from_planes(p0, p1):
+    """Natural R x C array from its two colour planes."""
+    p0 = np.asarray(p0)
+    p1 = np.asarray(p1)
+    R, H = p0.shape
+    out = np.empty((R, 2 * H), dtype=p0.dtype)
+    for r in range(R):
+        out[r, (r + 0) % 2::2] = p0[r]
+        out[r, (r + 1) % 2::2] = p1[r]
+    return out
+
+
+def ising_energy(s, b, w):
+    """E(s) = -sum_i b_i s_i - w sum over lattice edges of s_i s_j (FP64)."""
+    sf = np.asarray(s, dtype=np.float64)
+    bf = np.asarray(b, dtype=np.float64)
+    pairs = (sf[1:, :] * sf[:-1, :]).sum() + (sf[:, 1:] * sf[:, :-1]).sum()
+    return float(-(bf * sf).sum() - float(w) * pairs)
+
+
+def ising_half_sweep(s, b, w, color, u_plane):
+    """Update every site of colour `color` from its conditional.
+
+    s (R, C) uint8 spins, b (R, C) biases, w the coupling, u_plane (R, C // 2)
+    the colour's uniforms in plane order. Returns (new spins, P(s_i = 1) of
+    every site as computed here, in the natural layout)."""
+    s = np.asarray(s, dtype=np.uint8)
+    R, C = s.shape
+    sf = s.astype(np.float64)
+    n = np.zeros((R, C))
+    n[1:, :] += sf[:-1, :]          # neighbour above
+    n[:-1, :] += sf[1:, :]          # below
+    n[:, 1:] += sf[:, :-1]          # left
+    n[:, :-1] += sf[:, 1:]          # right
+    z = np.asarray(b, dtype=np.float64) + float(w) * n
+    with np.errstate(over="ignore"):
+        p = 1.0 / (1.0 + np.exp(-z))
+    u = np.zeros((R, C))
+    for r in range(R):
+        u[r, (r + color) % 2::2] = np.asarray(u_plane[r], dtype=np.float64)
+    rr, cc = np.indices((R, C))
+    mask = ((rr + cc) % 2) == color
+    out = s.copy()
+    out[mask] = (u < p)[mask].astype(np.uint8)
+    return out, p
+
+
+def ising_gibbs(s0, b, w, u):
+    """n sweeps (colour 0 then colour 1 each) from s0 with uniforms u of
+    shape (n, 2, R, C // 2). Returns the final spins and the number of
+    spins equal to 1 after every half-sweep, shape (n, 2)."""
+    s = np.asarray(s0, dtype=np.uint8).copy()
+    n = u.shape[0]
+    ones = np.zeros((n, 2), dtype=np.int64)
+    for t in range(n):
+        for c in range(2):
+            s, _ = ising_half_sweep(s, b, w, c, u[t, c])
+            ones[t, c] = int(s.sum(dtype=np.int64))
+    return s, ones

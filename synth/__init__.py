@@ -204,3 +204,38 @@ def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process with the given rate."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate, count))
+
+
+def ising_lattice(rows: int, cols: int, seed: int, flip: float = 0.1, eta: float = 1.0,
+                  w: float = 2.0):
+    """A noisy binary image for Ising denoising (§4.3.1): a smooth two-tone
+    pattern with a fraction `flip` of its pixels flipped at random, and the
+    biases of the +-1 denoising model (data strength eta, coupling J = w / 4)
+    written for {0, 1} spins: with sigma = 2s - 1, J sum sigma_i sigma_j +
+    eta sum sigma_i y'_i equals w sum s_i s_j + sum b_i s_i + const for
+    b_i = 2 eta y'_i - (w / 2) deg_i (y' = 2y - 1, deg_i the number of
+    lattice neighbours). Returns (y (rows, cols) uint8 noisy image,
+    b (rows, cols) float32, the clean image)."""
+    rng = np.random.default_rng(seed)
+    r = np.arange(rows, dtype=np.float32)[:, None]
+    c = np.arange(cols, dtype=np.float32)[None, :]
+    f1, f2, p1, p2 = rng.uniform(0.01, 0.05, 2).tolist() + rng.uniform(0.0, 6.28, 2).tolist()
+    clean = ((np.sin(f1 * r + p1) * np.sin(f2 * c + p2)) > 0).astype(np.uint8)
+    noise = rng.random((rows, cols), dtype=np.float32) < flip
+    y = np.where(noise, 1 - clean, clean).astype(np.uint8)
+    deg = np.full((rows, cols), 4.0, dtype=np.float32)
+    deg[0, :] -= 1
+    deg[-1, :] -= 1
+    deg[:, 0] -= 1
+    deg[:, -1] -= 1
+    b = (np.float32(2.0 * eta) * (2.0 * y.astype(np.float32) - 1.0) -
+         np.float32(w / 2.0) * deg).astype(np.float32)
+    return y, b, clean
+
+
+def ising_uniforms(n_sweeps: int, rows: int, cols: int, seed: int):
+    """Batch of uniforms for n_sweeps checkerboard sweeps: (n_sweeps, 2,
+    rows, cols // 2) float32 in [0, 1), colour-plane order. Both the oracle
+    and the device read this buffer."""
+    rng = np.random.default_rng(seed)
+    return rng.random((n_sweeps, 2, rows, cols // 2), dtype=np.float32)
