@@ -72,6 +72,8 @@ GROUPED_SOURCES = ["paper_1310_1537_gb300/csrc/glm_grouped.cu",
                    "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 SLICE_SOURCES = ["paper_1310_1537_gb300/csrc/glm_slice.cu",
                  "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
+ISING_SOURCES = ["paper_1310_1537_gb300/csrc/glm_ising.cu",
+                 "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 
 
 def kernel_source_hash(sources=None) -> str:
@@ -823,6 +825,107 @@ def run_slice(args, local):
     glm.glm_slice_destroy(sm)
 
 
+def run_ising(args, local):
+    """Checkerboard Gibbs sweeps of the square-lattice Ising model (§4.3.1):
+    an 8192 x 8192 denoising lattice, colour planes resident in HBM, one batch
+    of uniforms per sweep. Metric: site updates per second."""
+    import torch
+    import synth
+    import paper_1310_1537_gb300 as glm
+    torch.cuda.set_device(local)
+    rows = cols = 8192
+    w = 2.0
+    sweeps, warm = args.steps, args.warmup
+    seed = synth.seed_for(5)
+    y, b, _ = synth.ising_lattice(rows, cols, seed, w=w)
+    H = cols // 2
+    plane = rows * H
+    yd = torch.from_numpy(y).cuda()
+    bd = torch.from_numpy(b).cuda()
+    s0 = torch.empty((rows, H), dtype=torch.uint8, device="cuda")
+    s1 = torch.empty_like(s0)
+    b0 = torch.empty((rows, H), dtype=torch.float32, device="cuda")
+    b1 = torch.empty_like(b0)
+    glm.glm_ising_split(yd, 1, rows, cols, s0, s1)
+    glm.glm_ising_split(bd, 4, rows, cols, b0, b1)
+    # uniforms: drawn on the device by torch's generator (setup, not timed);
+    # the same (n, 2, rows, cols / 2) batch layout the oracle reads
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed + 1)
+    u = torch.rand((warm + sweeps, 2, rows, H), dtype=torch.float32, device="cuda", generator=gen)
+    ones = torch.zeros(2 * (warm + sweeps), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    glm.glm_ising_sweeps(s0, s1, b0, b1, rows, cols, w, warm, u[:warm], ones[:2 * warm], stream)
+    torch.cuda.synchronize()
+    sampler = _gpu_sampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    glm.glm_ising_sweeps(s0, s1, b0, b1, rows, cols, w, sweeps, u[warm:], ones[2 * warm:], stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    updates = rows * cols * sweeps
+    # the denoised fraction agreeing with the clean image (a sanity figure)
+    s_nat = torch.empty((rows, cols), dtype=torch.uint8, device="cuda")
+    glm.glm_ising_merge(s0, s1, 1, rows, cols, s_nat)
+    # end to end: each sweep's uniforms copied in from pinned host memory and
+    # its two counts of ones copied out
+    e2e_sweeps = min(sweeps, 4)
+    uh = u[warm:warm + e2e_sweeps].cpu().pin_memory()
+    ub = torch.empty((1, 2, rows, H), dtype=torch.float32, device="cuda")
+    oh = torch.empty(2 * e2e_sweeps, dtype=torch.int64).pin_memory()
+    ob = torch.empty(2, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_sweeps):
+        ub.copy_(uh[i:i + 1], non_blocking=True)
+        glm.glm_ising_sweeps(s0, s1, b0, b1, rows, cols, w, 1, ub, ob, stream)
+        oh[2 * i:2 * i + 2].copy_(ob, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    # the oracle: NumPy half-sweeps on a 2048 x 2048 corner of the lattice
+    import oracle
+    sr, sc = 2048, 2048
+    ys, bs = y[:sr, :sc], b[:sr, :sc]
+    us = synth.ising_uniforms(1, sr, sc, seed + 2)
+    reps, t1 = 0, time.perf_counter()
+    st = ys
+    while time.perf_counter() - t1 < 8.0 or reps < 1:
+        for c in (0, 1):
+            st, _ = oracle.ising_half_sweep(st, bs, w, c, us[0, c])
+        reps += 1
+    cpu_rate = reps * sr * sc / (time.perf_counter() - t1)
+    peak, peak_kind = measured_hbm_peak()
+    bytes_update = 4 + 4 + 1 + 1       # bias, uniform, spin written, other colour read
+    achieved = bytes_update * updates / (total_ms / 1e3) / 1e9
+    _emit({
+        "metric": "Ising site updates/s", "value": updates / (total_ms / 1e3),
+        "unit": "site updates/s", "n_gpus": 1, "steps": sweeps, "warmup": warm,
+        "ms_per_step": total_ms / sweeps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"checkerboard Gibbs, square-lattice Ising denoising: "
+                               f"{rows} x {cols} spins, w={w}, colour planes, batch uniforms",
+                   "step": "one sweep (two half-sweep launches)",
+                   "l2": "inputs larger than L2 (uniforms 268 MB per sweep), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak,
+                     "traffic": profile_traffic(os.path.join(ROOT, "profiles", "ising_big.md"),
+                                                ISING_SOURCES),
+                     "traffic_unit": "DRAM bytes per site update",
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_update": bytes_update},
+        "cpu_baseline": {"value": cpu_rate, "unit": "site updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{reps} NumPy sweeps of a {sr} x {sc} corner"},
+        "e2e": {"value": rows * cols * e2e_sweeps / e2e_s, "unit": "site updates/s",
+                "h2d_bytes_per_step": plane * 2 * 4, "d2h_bytes_per_step": 16,
+                "api": "glm_ising_sweeps per sweep with its uniforms copied in and the counts out"},
+        "clocks": clocks, "gpu_launches": 2 * sweeps,
+    })
+
+
 SERVING_RATE = 2000.0
 
 
@@ -995,7 +1098,7 @@ def main():
                     help="slice workload: shrinkage proposals per evaluation pass (0: 2)")
     ap.add_argument("--workload", default="big",
                     choices=["big", "small", "batched", "batched-fp8", "grouped", "serving",
-                             "slice"])
+                             "slice", "ising"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1010,6 +1113,7 @@ def main():
             return
         {"small": lambda: run_small(args, local),
          "slice": lambda: run_slice(args, local),
+         "ising": lambda: run_ising(args, local),
          "batched": lambda: run_batched(args, local),
          "batched-fp8": lambda: run_batched(args, local, fp8=True),
          "grouped": lambda: run_grouped(args, local),

@@ -471,6 +471,40 @@ GLM_API glm_status_t glm_slice_run(glm_slice_t s, const float *Xt, const uint8_t
 /* Synchronise the stream and return the sampler's device status. */
 GLM_API glm_status_t glm_slice_sync(glm_slice_t s, glm_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Square-lattice Ising model, checkerboard Gibbs sampling (§4.3.1).
+ * Spins s_i in {0, 1} on a rows x cols lattice (cols even), each node
+ * coupled to its 4 lattice neighbours with weight w, free boundary (a
+ * missing neighbour contributes nothing). Gibbs conditional:
+ * P(s_i = 1 | rest) = 1 / (1 + exp(-z_i)), z_i = b_i + w * sum_j s_j over
+ * the neighbours j of i (the energy is E(s) = -sum b_i s_i - w sum_<ij>
+ * s_i s_j). Colour c holds the sites with (row + col) % 2 == c; a sweep
+ * updates colour 0, then colour 1, setting s_i = 1 iff u_i < P(s_i = 1).
+ *
+ * Layout: each colour in its own dense plane of rows x (cols / 2) elements,
+ * plane entry (r, j) = site (r, 2j + (r + c) % 2) (the unit-stride colour
+ * layout of §4.3.1). All buffers are device memory owned by the caller.
+ * Spins must be 0 or 1.
+ * ---------------------------------------------------------------------- */
+
+/* Natural row-major rows x cols array (elem_bytes 1 or 4) into its two
+ * colour planes, and back. */
+GLM_API glm_status_t glm_ising_split(const void *nat, int32_t elem_bytes, int32_t rows, int32_t cols,
+                                     void *plane0, void *plane1, glm_stream_t stream);
+GLM_API glm_status_t glm_ising_merge(const void *plane0, const void *plane1, int32_t elem_bytes,
+                                     int32_t rows, int32_t cols, void *nat, glm_stream_t stream);
+
+/* n_sweeps checkerboard sweeps in place on the spin planes s0, s1 (uint8)
+ * with bias planes b0, b1 (FP32) and coupling w. u: the batch of uniforms in
+ * [0, 1), n_sweeps x 2 x rows x (cols / 2) FP32 (sweep, colour, then plane
+ * order). ones_out (optional, 8-byte aligned, n_sweeps x 2 int64): the number
+ * of 1s in plane c after half-sweep (t, c). Asynchronous: one launch per
+ * half-sweep. Unit-stride vector path when cols / 2 is a multiple of 8 and
+ * all planes and u are 16-byte aligned, else per-site. */
+GLM_API glm_status_t glm_ising_sweeps(uint8_t *s0, uint8_t *s1, const float *b0, const float *b1,
+                                      int32_t rows, int32_t cols, float w, int32_t n_sweeps,
+                                      const float *u, int64_t *ones_out, glm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

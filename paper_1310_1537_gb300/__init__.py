@@ -41,7 +41,7 @@ EXPORTS = (
     "glm_autotune_grouped", "glm_server_create", "glm_server_add_dataset", "glm_server_submit",
     "glm_server_poll", "glm_server_wait", "glm_server_stats", "glm_server_destroy",
     "glm_slice_create", "glm_slice_destroy", "glm_slice_eta", "glm_slice_coord_logpost",
-    "glm_slice_run", "glm_slice_sync",
+    "glm_slice_run", "glm_slice_sync", "glm_ising_split", "glm_ising_merge", "glm_ising_sweeps",
 )
 
 
@@ -133,6 +133,10 @@ def load(build_if_missing: bool = True):
                                  C.c_int32], st),
             "glm_server_stats": ([vp, C.POINTER(glm_server_stats_t)], st),
             "glm_server_destroy": ([vp], st),
+            "glm_ising_split": ([vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp], st),
+            "glm_ising_merge": ([vp, vp, C.c_int32, C.c_int32, C.c_int32, vp, vp], st),
+            "glm_ising_sweeps": ([vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float, C.c_int32, vp,
+                                  vp, vp], st),
             "glm_slice_create": ([C.POINTER(glm_slice_desc_t), C.POINTER(vp)], st),
             "glm_slice_destroy": ([vp], st),
             "glm_slice_eta": ([vp, vp, vp, vp, vp], st),
@@ -355,3 +359,22 @@ def glm_slice_run(s, Xt, y, eta, beta, f_state, init_f, n_sweeps, log_u0, uni, x
 
 def glm_slice_sync(s, stream=None) -> int:
     return int(load().glm_slice_sync(s, _stream(stream)))
+
+
+def glm_ising_split(nat, elem_bytes, rows, cols, plane0, plane1, stream=None) -> None:
+    """Natural row-major array -> its two checkerboard colour planes."""
+    _check(load().glm_ising_split(_ptr(nat), int(elem_bytes), int(rows), int(cols), _ptr(plane0),
+                                  _ptr(plane1), _stream(stream)), "glm_ising_split")
+
+
+def glm_ising_merge(plane0, plane1, elem_bytes, rows, cols, nat, stream=None) -> None:
+    """Two checkerboard colour planes -> the natural row-major array."""
+    _check(load().glm_ising_merge(_ptr(plane0), _ptr(plane1), int(elem_bytes), int(rows), int(cols),
+                                  _ptr(nat), _stream(stream)), "glm_ising_merge")
+
+
+def glm_ising_sweeps(s0, s1, b0, b1, rows, cols, w, n_sweeps, u, ones_out=None, stream=None) -> None:
+    """n_sweeps checkerboard Gibbs sweeps of the Ising model on the spin planes."""
+    _check(load().glm_ising_sweeps(_ptr(s0), _ptr(s1), _ptr(b0), _ptr(b1), int(rows), int(cols),
+                                   float(w), int(n_sweeps), _ptr(u), _ptr(ones_out), _stream(stream)),
+           "glm_ising_sweeps")

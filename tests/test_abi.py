@@ -131,3 +131,19 @@ def test_slice_sampler_rejects_bad_descriptors_without_a_device():
     assert lib.glm_slice_run(None, None, None, None, None, None, 0, 0, None, None, None, None,
                              None, None) == pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_slice_destroy(None) == pkg.GLM_OK
+
+
+def test_ising_entry_points_reject_bad_arguments_without_a_device():
+    lib = pkg.load()
+    # null pointers, odd or too-small sizes, bad element size: refused before
+    # any device call
+    assert lib.glm_ising_sweeps(None, None, None, None, 4, 8, 1.0, 1, None, None, None) == \
+        pkg.GLM_ERR_INVALID_ARG
+    for rows, cols, eb in [(0, 8, 1), (4, 7, 1), (4, 0, 1), (4, 8, 2)]:
+        assert lib.glm_ising_split(1, eb, rows, cols, 1, 1, None) == pkg.GLM_ERR_INVALID_ARG
+        assert lib.glm_ising_merge(1, 1, eb, rows, cols, 1, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_ising_sweeps(16, 16, 16, 16, 4, 8, 1.0, -1, 16, None, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_ising_sweeps(16, 16, 16, 16, 4, 8, float("nan"), 1, 16, None, None) == \
+        pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_ising_sweeps(16, 16, 16, 16, 4, 8, 1.0, 1, 16, 12, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_ising_sweeps(16, 16, 16, 16, 4, 8, 1.0, 0, None, None, None) == pkg.GLM_OK
