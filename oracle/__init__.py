@@ -21,6 +21,9 @@ Functions and the passages they follow:
   storage of X (bfloat16 RNE; OCP E4M3 with power-of-two column scales).
 * ``slice_step``, ``slice_gibbs`` — Gibbs sweeps of univariate slice sampling
   over the coefficients (§3.4.4), evaluated with the plain log-posterior.
+* ``logpost_grad_hess``    — f, g and the Hessian of the log-posterior
+  (§4.2's derivatives taken one order further, as §5.2 proposes):
+  H = -X^T diag(s(1 - s)) X - I / sigma^2 (NumPy, FP64).
 * ``ising_half_sweep``, ``ising_gibbs``, ``ising_energy``,
   ``ising_to_plane``, ``ising_from_planes`` — checkerboard Gibbs sampling of
   the square-lattice Ising model (§4.3.1) in the natural row-major layout
@@ -461,3 +464,27 @@ def ising_gibbs(s0, b, w, u):
             s, _ = ising_half_sweep(s, b, w, c, u[t, c])
             ones[t, c] = int(s.sum(dtype=np.int64))
     return s, ones
+
+
+# ---------------------------------------------------------------------------
+# Hessian of the Bayesian logistic log-posterior (§4.2 differentiated once
+# more; §5.2 names the Hessian as the next derivative to parallelise).
+# With mu_n = 1 / (1 + exp(-x_n . beta)): d^2 f / d beta d beta^T =
+# -sum_n mu_n (1 - mu_n) x_n x_n^T - I / sigma^2.
+
+
+def logpost_grad_hess(X, y, beta, prior_sigma=10.0, p=None):
+    """f (float), g (P,), H (P, P) of the log-posterior at one beta, FP64.
+    f and g are the plain-definition values of ``logpost_grad``."""
+    X = np.asarray(X, dtype=np.float64)
+    if p is not None:
+        X = X[:, :p]
+    P = X.shape[1]
+    b = np.asarray(beta, dtype=np.float64).reshape(P)
+    f, g = logpost_grad(X, y, b[None, :], prior_sigma=prior_sigma)
+    eta = X @ b
+    with np.errstate(over="ignore"):
+        mu = 1.0 / (1.0 + np.exp(-eta))
+    w = mu * (1.0 - mu)
+    H = -(X.T @ (w[:, None] * X)) - np.eye(P) / (prior_sigma * prior_sigma)
+    return float(f[0]), g[0], H
