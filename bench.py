@@ -72,6 +72,8 @@ GROUPED_SOURCES = ["paper_1310_1537_gb300/csrc/glm_grouped.cu",
                    "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 SLICE_SOURCES = ["paper_1310_1537_gb300/csrc/glm_slice.cu",
                  "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
+HESS_SOURCES = ["paper_1310_1537_gb300/csrc/glm_hess.cu",
+                "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 ISING_SOURCES = ["paper_1310_1537_gb300/csrc/glm_ising.cu",
                  "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 
@@ -926,6 +928,92 @@ def run_ising(args, local):
     })
 
 
+def run_hessian(args, local):
+    """One pass returning f, g and the Hessian (N = 2,000,000, P = 64, FP32,
+    one coefficient vector). CUDA-core FP32 arithmetic bound."""
+    import torch
+    import synth
+    import paper_1310_1537_gb300 as glm
+    torch.cuda.set_device(local)
+    n, p = 2_000_000, 64
+    d = synth.make_glm(n, p, synth.seed_for(6), dtype=np.float32)
+    Xd = torch.from_numpy(d.X).cuda()
+    yd = torch.from_numpy(d.y).cuda()
+    bd = torch.from_numpy(d.beta_star.astype(np.float32)).cuda()
+    f = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(p, dtype=torch.float32, device="cuda")
+    H = torch.empty((p, p), dtype=torch.float32, device="cuda")
+    h = glm.glm_hess_create(n, p, p)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        glm.glm_hess_eval(h, Xd, yd, bd, f, g, H, stream)
+    assert glm.glm_hess_sync(h, stream) == glm.GLM_OK
+    sampler = _gpu_sampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        glm.glm_hess_eval(h, Xd, yd, bd, f, g, H, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    assert glm.glm_hess_sync(h, stream) == glm.GLM_OK
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # end to end: beta in from pinned host memory, f, g and H out, synchronised
+    bh = torch.from_numpy(d.beta_star.astype(np.float32)).pin_memory()
+    fh = torch.empty(1, dtype=torch.float64).pin_memory()
+    gh = torch.empty(p, dtype=torch.float32).pin_memory()
+    Hh = torch.empty((p, p), dtype=torch.float32).pin_memory()
+    reps = 50
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        bd.copy_(bh, non_blocking=True)
+        glm.glm_hess_eval(h, Xd, yd, bd, f, g, H, stream)
+        fh.copy_(f, non_blocking=True)
+        gh.copy_(g, non_blocking=True)
+        Hh.copy_(H, non_blocking=True)
+        stream.synchronize()
+    e2e = reps / (time.perf_counter() - t0)
+    glm.glm_hess_destroy(h)
+    # the oracle on a row sample, scaled to N
+    import oracle
+    rows = 200_000
+    X64 = d.X[:rows].astype(np.float64)
+    b64 = d.beta_star.astype(np.float64)
+    k, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < 8.0 or k < 2:
+        oracle.logpost_grad_hess(X64, d.y[:rows], b64)
+        k += 1
+    cpu = 1.0 / ((time.perf_counter() - t1) / k * n / rows)
+    flops = n * (2 * p + 2 * p + p * (p + 1))     # eta, g, upper triangle of X^T W X
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12           # FP32 FMA lanes x 2 FLOP x max SM clock
+    achieved = flops / (ms / 1e3) / 1e12
+    _emit({
+        "metric": "log-posterior+grad+Hessian evals/s", "value": 1e3 / ms, "unit": "evals/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"one-pass f, g, Hessian: N={n}, P={p}, X FP32 row-major, K=1",
+                   "l2": "inputs larger than L2 (X 512 MB), no flush",
+                   "hbm_bytes_per_eval": n * p * 4 + n},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "traffic": profile_traffic(os.path.join(ROOT, "profiles", "hess_big.md"),
+                                                HESS_SOURCES),
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                     "algorithmic_flops_per_eval": flops},
+        "cpu_baseline": {"value": cpu, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{k} NumPy evaluations on rows [0, {rows}), scaled to N={n}"},
+        "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": p * 4,
+                "d2h_bytes_per_step": 8 + p * 4 + p * p * 4,
+                "api": "glm_hess_eval with beta in and f, g, H out, synced"},
+        "clocks": clocks, "gpu_launches": 2 * args.steps,
+    })
+
+
 SERVING_RATE = 2000.0
 
 
@@ -1098,7 +1186,7 @@ def main():
                     help="slice workload: shrinkage proposals per evaluation pass (0: 2)")
     ap.add_argument("--workload", default="big",
                     choices=["big", "small", "batched", "batched-fp8", "grouped", "serving",
-                             "slice", "ising"])
+                             "slice", "ising", "hessian"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1114,6 +1202,7 @@ def main():
         {"small": lambda: run_small(args, local),
          "slice": lambda: run_slice(args, local),
          "ising": lambda: run_ising(args, local),
+         "hessian": lambda: run_hessian(args, local),
          "batched": lambda: run_batched(args, local),
          "batched-fp8": lambda: run_batched(args, local, fp8=True),
          "grouped": lambda: run_grouped(args, local),

@@ -505,6 +505,32 @@ GLM_API glm_status_t glm_ising_sweeps(uint8_t *s0, uint8_t *s1, const float *b0,
                                       int32_t rows, int32_t cols, float w, int32_t n_sweeps,
                                       const float *u, int64_t *ones_out, glm_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Log-posterior, gradient and Hessian in one pass (§4.2's derivatives one
+ * order further, which §5.2 proposes for Newton-type and Riemannian
+ * samplers), one coefficient vector, FP32 X with P <= 64:
+ *   f, g as glm_logpost_grad (prior N(0, s^2 I));
+ *   H = -X^T diag(mu (1 - mu)) X - I / s^2, mu_n = 1 / (1 + exp(-x_n . beta)).
+ * ---------------------------------------------------------------------- */
+typedef struct glm_hess *glm_hess_t;
+
+/* A Hessian evaluator for N x P row-major FP32 X with row stride ld
+ * (P <= ld <= 64, ld a multiple of 4): per-CTA partials are allocated here. */
+GLM_API glm_status_t glm_hess_create(int64_t n_rows, int32_t p, int32_t ld, double prior_sigma,
+                                     int32_t device, glm_hess_t *out);
+GLM_API glm_status_t glm_hess_destroy(glm_hess_t h);
+
+/* f_out (1 FP64), g_out (P FP32), H_out (P x P FP32 row-major, symmetric) at
+ * beta (P FP32), all device memory; X 16-byte aligned, y N bytes in {0, 1}.
+ * Asynchronous: one pass over X plus a fixed-order combine (deterministic). */
+GLM_API glm_status_t glm_hess_eval(glm_hess_t h, const float *X, const uint8_t *y,
+                                   const float *beta, double *f_out, float *g_out, float *H_out,
+                                   glm_stream_t stream);
+
+/* Synchronise the stream and return the evaluator's device status
+ * (GLM_ERR_TIMEOUT if a bounded wait expired; the results are then NaN). */
+GLM_API glm_status_t glm_hess_sync(glm_hess_t h, glm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

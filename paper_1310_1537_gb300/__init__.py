@@ -42,6 +42,7 @@ EXPORTS = (
     "glm_server_poll", "glm_server_wait", "glm_server_stats", "glm_server_destroy",
     "glm_slice_create", "glm_slice_destroy", "glm_slice_eta", "glm_slice_coord_logpost",
     "glm_slice_run", "glm_slice_sync", "glm_ising_split", "glm_ising_merge", "glm_ising_sweeps",
+    "glm_hess_create", "glm_hess_destroy", "glm_hess_eval", "glm_hess_sync",
 )
 
 
@@ -133,6 +134,11 @@ def load(build_if_missing: bool = True):
                                  C.c_int32], st),
             "glm_server_stats": ([vp, C.POINTER(glm_server_stats_t)], st),
             "glm_server_destroy": ([vp], st),
+            "glm_hess_create": ([C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                 C.POINTER(vp)], st),
+            "glm_hess_destroy": ([vp], st),
+            "glm_hess_eval": ([vp, vp, vp, vp, vp, vp, vp, vp], st),
+            "glm_hess_sync": ([vp, vp], st),
             "glm_ising_split": ([vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp], st),
             "glm_ising_merge": ([vp, vp, C.c_int32, C.c_int32, C.c_int32, vp, vp], st),
             "glm_ising_sweeps": ([vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_float, C.c_int32, vp,
@@ -378,3 +384,24 @@ def glm_ising_sweeps(s0, s1, b0, b1, rows, cols, w, n_sweeps, u, ones_out=None, 
     _check(load().glm_ising_sweeps(_ptr(s0), _ptr(s1), _ptr(b0), _ptr(b1), int(rows), int(cols),
                                    float(w), int(n_sweeps), _ptr(u), _ptr(ones_out), _stream(stream)),
            "glm_ising_sweeps")
+
+
+def glm_hess_create(n_rows, p, ld, prior_sigma=10.0, device=0):
+    """Evaluator of f, g and the Hessian for N x P row-major FP32 X (P <= ld <= 64)."""
+    h = C.c_void_p()
+    _check(load().glm_hess_create(int(n_rows), int(p), int(ld), float(prior_sigma), int(device),
+                                  C.byref(h)), "glm_hess_create")
+    return h.value
+
+
+def glm_hess_destroy(h) -> None:
+    _check(load().glm_hess_destroy(h), "glm_hess_destroy")
+
+
+def glm_hess_eval(h, X, y, beta, f_out, g_out, H_out, stream=None) -> None:
+    _check(load().glm_hess_eval(h, _ptr(X), _ptr(y), _ptr(beta), _ptr(f_out), _ptr(g_out),
+                                _ptr(H_out), _stream(stream)), "glm_hess_eval")
+
+
+def glm_hess_sync(h, stream=None) -> int:
+    return load().glm_hess_sync(h, _stream(stream))

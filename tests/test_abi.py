@@ -147,3 +147,16 @@ def test_ising_entry_points_reject_bad_arguments_without_a_device():
         pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_ising_sweeps(16, 16, 16, 16, 4, 8, 1.0, 1, 16, 12, None) == pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_ising_sweeps(16, 16, 16, 16, 4, 8, 1.0, 0, None, None, None) == pkg.GLM_OK
+
+
+def test_hessian_evaluator_rejects_bad_shapes_without_a_device():
+    import ctypes as C
+    lib = pkg.load()
+    h = C.c_void_p()
+    for n, p, ld, s in [(-1, 4, 4, 1.0), (10, 0, 4, 1.0), (10, 65, 68, 1.0), (10, 8, 6, 1.0),
+                        (10, 8, 4, 1.0), (10, 8, 68, 1.0), (10, 8, 8, 0.0), (10, 8, 8, float("inf"))]:
+        assert lib.glm_hess_create(n, p, ld, s, 0, C.byref(h)) == pkg.GLM_ERR_INVALID_ARG
+        assert h.value is None
+    assert lib.glm_hess_create(10, 8, 8, 1.0, 0, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_hess_eval(None, None, None, None, None, None, None, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_hess_destroy(None) == pkg.GLM_OK
