@@ -11,13 +11,13 @@
 // threads per row, forms eta, w = mu (1 - mu), r = y - mu and the
 // log-likelihood term; phase B1, thread j < P, adds sum_n r_n x_nj to its g_j;
 // phase B2, one thread per (8 x 4 block of the upper triangle of X^T W X,
-// group of every third row) adds sum_n (w_n x_n,i..i+7) (x_n,j..j+3)^T over
+// group of every third row) adds sum_n (x_n,i..i+7) (w_n x_n,j..j+3)^T over
 // its rows to 32 register accumulators (three 16-byte shared loads per 32
 // FMAs); the remaining threads do phase B1, g_j += sum_n r_n x_nj. At the end
 // the three row groups' sums are added in a fixed order through shared
 // memory, the CTA's sums are written once as partials and a second kernel
-// adds them in a fixed order (deterministic), adds the prior and fills the
-// symmetric H.
+// adds them in a fixed order in FP64 (deterministic), adds the prior and
+// fills the symmetric H.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -169,11 +169,18 @@ __global__ void __launch_bounds__(kHessThreads, 3) hess_kernel(HessParams p)
             ptx::fence_proxy_async_smem();                  // before any later copy into the slot
         }
         __syncthreads();
-        // ---- phase A: eta, w, r, ell (4 threads per row, 16 columns each) ----
+        // ---- phase A: eta, w, r, ell (4 threads per row) ---------------------------
+        // thread aq takes the row's 16-byte chunks aq, aq + 4, aq + 8, aq + 12,
+        // in an order rotated by the row, so that the two rows of each 8-lane
+        // shared-memory access use different bank groups
         {
             const float *xr = xt + arow * ld;
             float pa = 0.0f;
-            for (int c = aq * 16; c < aq * 16 + 16 && c < ld && c < kHessMaxP; c += 4) {
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int c = 4 * (aq + 4 * ((cc + arow) & 3));     // first column of the chunk
+                if (c >= ld)
+                    continue;
                 const float4 xv = *reinterpret_cast<const float4 *>(xr + c);
                 pa = fmaf(xv.x, bs[c], pa);
                 pa = fmaf(xv.y, bs[c + 1], pa);
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(kHessThreads, 3) hess_kernel(HessParams p)
                 }
             }
         }
-        // ---- phase B2: H block += sum_n (w_n x_n,i) (x_n,j)^T ---------------------
+        // ---- phase B2: H block += sum_n (x_n,i) (w_n x_n,j)^T ---------------------
         if (b2) {
             const float *xi = xt + 8 * bi;   // may read past column P (into the next row or the
             const float *xj = xt + 4 * bj;   // ring's slack): those entries are never combined
@@ -224,9 +231,8 @@ __global__ void __launch_bounds__(kHessThreads, 3) hess_kernel(HessParams p)
                 const float4 a1 = *reinterpret_cast<const float4 *>(xi + n * ld + 4);
                 const float4 c4 = *reinterpret_cast<const float4 *>(xj + n * ld);
                 const float wn = ws[n];
-                const float a[8] = {wn * a0.x, wn * a0.y, wn * a0.z, wn * a0.w,
-                                    wn * a1.x, wn * a1.y, wn * a1.z, wn * a1.w};
-                const float c[4] = {c4.x, c4.y, c4.z, c4.w};
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float c[4] = {wn * c4.x, wn * c4.y, wn * c4.z, wn * c4.w};
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -280,45 +286,78 @@ __global__ void __launch_bounds__(kHessThreads, 3) hess_kernel(HessParams p)
     }
 }
 
-// Fixed-order sums of the CTAs' partials, prior, symmetric H.
-__global__ void hess_combine_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g,
-                                    const float *__restrict__ part_h, int parts, int P,
-                                    const float *__restrict__ beta, double inv_s2, double prior_const,
-                                    double *__restrict__ f_out, float *__restrict__ g_out,
-                                    float *__restrict__ H_out)
+// Fixed-order sums of the CTAs' partials, prior, symmetric H. A block takes
+// 32 consecutive output elements; its 8 warps each add a contiguous range of
+// CTAs (all loads of a range in flight, coalesced over the elements), then
+// warp 0 adds the 8 range sums in order.
+constexpr int kHessRedWarps = 8;
+
+__global__ void __launch_bounds__(32 * kHessRedWarps)
+    hess_combine_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g,
+                        const float *__restrict__ part_h, int parts, int P,
+                        const float *__restrict__ beta, double inv_s2, double prior_const,
+                        double *__restrict__ f_out, float *__restrict__ g_out,
+                        float *__restrict__ H_out)
 {
+    __shared__ double sum[kHessRedWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int PB = (P + 3) / 4;
     const int NB = hess_nblocks(PB);
     const int nel = 1 + P + NB * kHessBlockElems;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nel; e += gridDim.x * blockDim.x) {
-        if (e == 0) {
-            double v = 0.0, bb = 0.0;
-            for (int q = 0; q < parts; ++q)
-                v += part_f[q];
-            for (int j = 0; j < P; ++j)
-                bb += (double)beta[j] * (double)beta[j];
-            *f_out = v - 0.5 * inv_s2 * bb - prior_const;
-        } else if (e <= P) {
-            const int j = e - 1;
-            float v = 0.0f;
-            for (int q = 0; q < parts; ++q)
-                v += part_g[(size_t)q * kHessMaxP + j];
-            g_out[j] = v - beta[j] * (float)inv_s2;
-        } else {
-            const int k = e - 1 - P;
-            const int blk = k / kHessBlockElems, u = (k % kHessBlockElems) >> 2, v2 = k & 3;
-            int I = 0, J = 0;
-            hess_block(blk, PB, I, J);
-            const int i = 8 * I + u, j = 4 * J + v2;
-            if (i >= P || j >= P || j < i)
-                continue;                                   // outside P, or mirrored from j >= i
-            float v = 0.0f;
-            for (int q = 0; q < parts; ++q)
-                v += part_h[((size_t)q * kHessMaxBlocks + blk) * kHessBlockElems + 4 * u + v2];
-            const float hv = -v - (i == j ? (float)inv_s2 : 0.0f);
-            H_out[(size_t)i * P + j] = hv;
-            H_out[(size_t)j * P + i] = hv;
+    const int e = blockIdx.x * 32 + lane;
+    const int per = (parts + kHessRedWarps - 1) / kHessRedWarps;
+    const int q0 = warp * per;
+    const int q1 = q0 + per < parts ? q0 + per : parts;
+    double v = 0.0;
+    if (e < nel) {
+        for (int qb = q0; qb < q1; qb += 16) {
+            double buf[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int q = qb + u;
+                double t = 0.0;
+                if (q < q1) {
+                    if (e == 0)
+                        t = part_f[q];
+                    else if (e <= P)
+                        t = (double)part_g[(size_t)q * kHessMaxP + e - 1];
+                    else
+                        t = (double)part_h[(size_t)q * kHessMaxBlocks * kHessBlockElems + (e - 1 - P)];
+                }
+                buf[u] = t;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                v += buf[u];
         }
+    }
+    sum[warp][lane] = v;
+    __syncthreads();
+    if (warp != 0 || e >= nel)
+        return;
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < kHessRedWarps; ++w)
+        tot += sum[w][lane];
+    if (e == 0) {
+        double bb = 0.0;
+        for (int j = 0; j < P; ++j)
+            bb += (double)beta[j] * (double)beta[j];
+        *f_out = tot - 0.5 * inv_s2 * bb - prior_const;
+    } else if (e <= P) {
+        const int j = e - 1;
+        g_out[j] = (float)tot - beta[j] * (float)inv_s2;
+    } else {
+        const int k = e - 1 - P;
+        const int blk = k / kHessBlockElems, u = (k % kHessBlockElems) >> 2, v2 = k & 3;
+        int I = 0, J = 0;
+        hess_block(blk, PB, I, J);
+        const int i = 8 * I + u, j = 4 * J + v2;
+        if (i >= P || j >= P || j < i)
+            return;                                         // outside P, or mirrored from j >= i
+        const float hv = -(float)tot - (i == j ? (float)inv_s2 : 0.0f);
+        H_out[(size_t)i * P + j] = hv;
+        H_out[(size_t)j * P + i] = hv;
     }
 }
 
@@ -422,7 +461,7 @@ glm_status_t glm_hess_eval(glm_hess_t h, const float *X, const uint8_t *y, const
     hess_kernel<<<h->grid, kHessThreads, smem, st>>>(p);
     const double s2 = h->prior_sigma * h->prior_sigma;
     const int nel = 1 + h->p + hess_nblocks((h->p + 3) / 4) * kHessBlockElems;
-    hess_combine_kernel<<<(nel + 255) / 256, 256, 0, st>>>(
+    hess_combine_kernel<<<(nel + 31) / 32, 32 * kHessRedWarps, 0, st>>>(
         h->part_f, h->part_g, h->part_h, h->grid, h->p, beta, 1.0 / s2,
         0.5 * h->p * std::log(2.0 * M_PI * s2), f_out, g_out, H_out);
     return cudaGetLastError() == cudaSuccess ? GLM_OK : GLM_ERR_CUDA;
