@@ -3,9 +3,10 @@
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 benchmark's ``cpu_baseline`` / ``--impl reference`` legs may import this
 package; the library under ``paper_1310_1537_gb300`` never does. The oracle
-shares no code with the CUDA path. The arithmetic lives in ``glm_oracle.c``
-(plain single-threaded C, FP64); this module only compiles it with gcc and
-marshals numpy arrays through ctypes.
+shares no code with the CUDA path. The GLM arithmetic lives in
+``glm_oracle.c`` (plain single-threaded C, FP64), which this module compiles
+with gcc and calls through ctypes; the slice sampler, the Ising sampler and
+the Hessian are plain NumPy FP64 below.
 
 Functions and the passages they follow:
 
