@@ -280,8 +280,14 @@ GLM_API glm_status_t glm_selftest_wait_timeout(glm_handle_t h, int32_t spin_limi
  *
  * Set-up. The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. A bounded device wait that expires shows up as
- * NaN results.
+ * before any stream capture. The address is kept per device together with
+ * the CUDA context it belongs to: after cudaDeviceReset (a new context) the
+ * next call looks it up again, so that call is a set-up call too.
+ *
+ * Errors: as glm_create and glm_logpost_grad (GLM_ERR_INVALID_ARG for a
+ * non-finite prior_sigma or misaligned pointers; GLM_ERR_UNSUPPORTED for
+ * rows wider than 1 MiB), nothing launched. A bounded device wait that
+ * expires shows up as NaN results.
  */
 GLM_API glm_status_t glm_logpost_grad_noalloc(const void *X, const float *x_scale,
                                               const uint8_t *y, int64_t n_rows, int32_t p,

@@ -30,14 +30,6 @@ static int elem_bytes_of(int xtype)
     }
 }
 
-static int env_int(const char *name, int dflt)
-{
-    const char *v = std::getenv(name);
-    if (!v || !*v)
-        return dflt;
-    return std::atoi(v);
-}
-
 glm_status_t launch_fused(glm_ctx *h, const FusedParams &p, int kc, cudaStream_t s)
 {
     switch (h->d.xtype) {
@@ -83,7 +75,7 @@ glm_status_t fused_configure(glm_ctx *h)
     // comes from a 2-D tensor copy of 8-byte words whose box is wider than the
     // row (box dimensions are at most 256 elements, so rows up to 2032 bytes).
     const bool pad_ok = h->d.n_rows > 0 && pc % 2 == 0 && row_bytes + 16 <= 256 * 8 &&
-                        env_int("GLM_FUSED_NO_PAD", 0) == 0 && tensor_map_encoder() != nullptr;
+                        tensor_map_encoder() != nullptr;
     auto srow_for = [&](int sp) { return (pad_ok && sp != 32) ? row_bytes + 16 : row_bytes; };
     // Fewest threads per row whose one-batch tile still fits two stages:
     // bigger tiles amortise the per-tile barriers and label loads.
@@ -94,16 +86,10 @@ glm_status_t fused_configure(glm_ctx *h)
             break;
         }
     }
-    const int fs = env_int("GLM_FUSED_SPLIT", 0);
-    if (fs == 1 || fs == 2 || fs == 4 || fs == 32)
-        split = fs;
-    int per_sm = env_int("GLM_FUSED_CTAS_PER_SM", 1);
-    if (per_sm < 1 || per_sm > 4)
-        per_sm = 1;
-    const int budget = kSmemOptin / per_sm - (per_sm > 1 ? 1024 : 0);
+    const int budget = kSmemOptin;
     int rb = kFusedThreads / split;
     int srow = srow_for(split);
-    int target = env_int("GLM_FUSED_STAGE_BYTES", 49152);
+    const int target = 49152;
     // rows per tile: a multiple of the phase-1 batch, at most four batches
     auto pick_rows = [&](int rbv) {
         int t = (target / srow) / rbv * rbv;
@@ -114,12 +100,6 @@ glm_status_t fused_configure(glm_ctx *h)
         return t;
     };
     int T = pick_rows(rb);
-    const int ft = env_int("GLM_FUSED_TILE_ROWS", 0);
-    if (ft > 0) {
-        T = (ft + rb - 1) / rb * rb;
-        if (T > 4 * rb)
-            T = 4 * rb;
-    }
     int stages = kMaxStages;
     while (stages >= 2 && fused_smem_total(h, T, stages, h->kc_max, srow) > budget)
         --stages;
@@ -134,9 +114,6 @@ glm_status_t fused_configure(glm_ctx *h)
     }
     if (stages < 2)
         return GLM_ERR_UNSUPPORTED;
-    const int fst = env_int("GLM_FUSED_STAGES", 0);
-    if (fst >= 2 && fst <= stages)
-        stages = fst;
     h->split = split;
     h->stages = stages;
     h->tile_rows = T;
@@ -151,11 +128,8 @@ glm_status_t fused_configure(glm_ctx *h)
     }
     h->fx_map_ptr = nullptr;
     h->smem_bytes = fused_smem_total(h, T, stages, h->kc_max, srow);
-    h->grid = h->sm_count * per_sm;
-    h->use_pdl = env_int("GLM_NO_PDL", 0) ? 0 : 1;
-    const int g = env_int("GLM_FUSED_GRID", 0);
-    if (g > 0 && g <= 4096)
-        h->grid = g;
+    h->grid = h->sm_count;
+    h->use_pdl = 1;
     return GLM_OK;
 }
 

@@ -778,12 +778,6 @@ __global__ void __launch_bounds__(kNarrowMaxThreads, 1)
 
 // ---------------------------------------------------------------------------
 
-static int env_int(const char *name, int dflt)
-{
-    const char *v = std::getenv(name);
-    return (v && *v) ? std::atoi(v) : dflt;
-}
-
 // Narrow-row path: chunks per row when at most 32 columns are used, else 0.
 static int grouped_nch(int p, int epc)
 {
@@ -814,21 +808,12 @@ glm_status_t grouped_configure(glm_ctx *h)
         return GLM_ERR_UNSUPPORTED;
     const int row_bytes = h->d.ld * es;
     const int pcue = pcu * epc;
-    const bool narrow_ok = grouped_nch(h->d.p, epc) > 0;
-    const bool narrow = narrow_ok && env_int("GLM_GROUPED_NARROW", 0) != 0;
-    int warps = env_int("GLM_GROUPED_WARPS", narrow ? 12 : 16);
-    if (warps < 1 || warps > (narrow ? kNarrowMaxThreads : kGroupedMaxThreads) / 32)
-        warps = narrow ? 12 : 16;
-    int per_sm = env_int("GLM_GROUPED_CTAS_PER_SM", 1);
-    if (per_sm < 1 || per_sm > 4)
-        per_sm = 1;
-    const int budget = kSmemOptinBytes / per_sm - (per_sm > 1 ? 1024 : 0);
-    // 32-row units per TMA slot (narrow rows only): bigger slots keep more
-    // bytes in flight per warp
-    int units = narrow ? (kGroupedRows * row_bytes <= 4096 ? 2 : 1) : 1;
-    const int fu = env_int("GLM_GROUPED_UNITS", 0);
-    if (narrow && (fu == 1 || fu == 2 || fu == 4))
-        units = fu;
+    // the default is the warp-stream kernel; the autotuner also tries the
+    // narrow-row kernel where it applies
+    const bool narrow = false;
+    int warps = 16;
+    const int budget = kSmemOptinBytes;
+    const int units = 1;
     int stages = 8;
     while (stages >= 2 && grouped_smem(row_bytes, warps, stages, pcue, narrow, units) > budget)
         --stages;
@@ -840,14 +825,11 @@ glm_status_t grouped_configure(glm_ctx *h)
     }
     if (stages < 2)
         return GLM_ERR_UNSUPPORTED;
-    const int fst = env_int("GLM_GROUPED_STAGES", 0);
-    if (fst >= 2 && fst <= stages)
-        stages = fst;
     h->gr_warps = warps;
     h->gr_stages = stages;
     h->gr_units = units;
     h->gr_narrow = narrow ? 1 : 0;
-    h->gr_grid = h->sm_count * per_sm;
+    h->gr_grid = h->sm_count;
     return GLM_OK;
 }
 

@@ -9,6 +9,7 @@
 // this entry point instead keeps its scratch (the cross-CTA fixed-point
 // accumulators, the completion ticket and the flag/status words) in one
 // file-scope device array of a fixed size, so a call allocates nothing.
+#include <cuda.h>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -31,20 +32,48 @@ constexpr size_t kScratchWords = kAccWords + 32;
 static __device__ __align__(256) unsigned long long g_glm_noalloc_scratch[kScratchWords];
 
 std::mutex g_setup_mutex;
-void *g_scratch_addr[kNoAllocMaxDevices];   // device address per device, set once
+void *g_scratch_addr[kNoAllocMaxDevices];   // device address per device
+void *g_scratch_ctx[kNoAllocMaxDevices];    // the context that address belongs to
 
-// Look up (once per device, with that device current) the device address of
-// the scratch array.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    return fn;
+}
+
+// Look up, with the device current, the device address of the scratch array:
+// once per device, and again only if the device's context has changed since
+// (after cudaDeviceReset the module is loaded anew and the array may move).
 glm_status_t scratch_for_device(int dev, void **out)
 {
+    CtxGetCurrentFn get = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (!get || get(&ctx) != CUDA_SUCCESS)
+        return GLM_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || !ctx || g_scratch_ctx[dev] != (void *)ctx) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_glm_noalloc_scratch) != cudaSuccess || !ptr) {
             cudaGetLastError();
             return GLM_ERR_CUDA;
         }
+        // the runtime makes the primary context current on first use: read it again
+        if (get(&ctx) != CUDA_SUCCESS)
+            return GLM_ERR_CUDA;
         g_scratch_addr[dev] = ptr;
+        g_scratch_ctx[dev] = (void *)ctx;
     }
     *out = g_scratch_addr[dev];
     return GLM_OK;
@@ -63,18 +92,20 @@ extern "C" glm_status_t glm_logpost_grad_noalloc(const void *X, const float *x_s
                                                  const float *beta, int32_t K, double *f_out,
                                                  float *g_out, glm_stream_t stream)
 {
+    // the same checks as glm_create and glm_logpost_grad
+    auto misaligned = [](const void *q, uintptr_t a) { return reinterpret_cast<uintptr_t>(q) % a != 0; };
     const int es = elem_bytes(xtype);
     if (es == 0 || n_rows < 0 || p < 1 || ld < p || K < 1 || K > 1024 ||
-        !(prior_sigma > 0.0) || !beta || !f_out || !g_out)
+        !(prior_sigma > 0.0) || !std::isfinite(prior_sigma) || !beta || !f_out || !g_out)
         return GLM_ERR_INVALID_ARG;
     if (p > kNoAllocMaxP)
         return GLM_ERR_INVALID_ARG;        // the fixed scratch holds P <= 1024 only
     if (((int64_t)ld * es) % 16 != 0 || (n_rows > 0 && (!X || !y)) ||
-        (X && reinterpret_cast<uintptr_t>(X) % 16 != 0) ||
-        (xtype == GLM_X_FP8E4M3) != (x_scale != nullptr) ||
-        reinterpret_cast<uintptr_t>(f_out) % 8 != 0)
+        (X && misaligned(X, 16)) || (xtype == GLM_X_FP8E4M3) != (x_scale != nullptr) ||
+        (x_scale && misaligned(x_scale, 4)) || misaligned(beta, 4) || misaligned(f_out, 8) ||
+        misaligned(g_out, 4))
         return GLM_ERR_INVALID_ARG;
-    if (n_rows > ((int64_t)1 << 40))
+    if (n_rows > ((int64_t)1 << 40) || (int64_t)ld * es > (1 << 20))
         return GLM_ERR_UNSUPPORTED;
 
     int dev = 0;

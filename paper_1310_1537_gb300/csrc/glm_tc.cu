@@ -6,9 +6,9 @@
 // with TMA (128B swizzle, 2-4 stages) and, from the same staged tile,
 //   MMA1: D1[2K x 128] = B1 . X_tile^T   (A = B1 in tensor memory: rows 2k and
 //         2k+1 hold the bf16 hi and lo parts of beta_k; B = the tile, K-major)
-//   epilogue (8 warps): lane n of D1 belongs to vector k = n/2; the two lanes
-//         of a vector add their hi and lo products (one shuffle) to get eta
-//         for 64 rows, each takes 32 of them through the TR map (ell, r),
+//   epilogue (16 warps): lane n of D1 belongs to vector k = n/2; the two
+//         lanes of a vector add their hi and lo products (one shuffle) to get
+//         eta for 32 rows, each takes 16 of them through the TR map (ell, r),
 //         accumulates f, splits r into bf16 hi + lo and writes them to the
 //         R tile in shared memory
 //   MMA2: D2[P x 2K] += X_tile^T . R_tile   (both operands MN-major)
@@ -18,7 +18,7 @@
 // while X stays in 2-byte storage. Per-CTA partials are combined by a second
 // kernel in a fixed order (deterministic).
 //
-// FP8 E4M3 storage: every E4M3 value is exactly an FP16 normal, so two
+// FP8 E4M3 storage: every E4M3 value is exactly an FP16 normal, so four
 // converter warps turn each staged E4M3 tile into FP16 in the same swizzled
 // layout (one cvt per pair of values) and the MMAs run with FP16 operands;
 // beta and r are split into FP16 hi + lo terms. The column scales fold into
@@ -53,7 +53,7 @@ constexpr int kTcConvWarps = 4;                     // FP8 tile converters
 constexpr int kTcThreadsFp8 = kTcThreads + 32 * kTcConvWarps;
 constexpr int kTcMaxStages = 4;
 constexpr int kTcRawRows = 64;                      // rows per staged E4M3 slot (half a tile)
-constexpr int kTcMaxRawStages = 3;
+constexpr int kTcMaxRawStages = 4;                  // even: RS/2 slots per half tile
 constexpr int kTcMaxP = 256;
 constexpr int kTcMaxKB = 64;
 constexpr int kTcTmemCols = 512;
@@ -469,8 +469,10 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                 // wider than stored (the extra chunk is outside the tensor: zero fill)
                 const unsigned bytes = (unsigned)(kTcRawRows * raw_row);
                 for (int u = 0; u < 2 * nt; ++u) {
-                    const int s = u % RS;
-                    const int use = u / RS;
+                    // each half tile has its own RS/2 slots, so every waiter
+                    // on a slot has consumed that slot's previous use
+                    const int s = (u & 1) + 2 * ((u >> 1) % (RS / 2));
+                    const int use = (u >> 1) / (RS / 2);
                     if (use > 0 && !ptx::mbar_wait_bounded(&raw_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
                         atomicOr(p.status, kDevTimeout);
                         s_abort = 1;
@@ -555,10 +557,9 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
         const uint32_t rx = (uint32_t)(r & 7);
         bool ok = true;
         for (int i = 0; i < nt; ++i) {
-            const int u = 2 * i + half;
-            const int rs = u % RS;
+            const int rs = half + 2 * (i % (RS / 2));
             const int s = i % stages;
-            ok = ptx::mbar_wait_bounded(&raw_full[rs], (unsigned)(u / RS) & 1u, kSpinLimit);
+            ok = ptx::mbar_wait_bounded(&raw_full[rs], (unsigned)(i / (RS / 2)) & 1u, kSpinLimit);
             if (ok && i >= stages)
                 ok = ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(i / stages - 1) & 1u, kSpinLimit);
             if (!ok)
@@ -861,15 +862,16 @@ __global__ void __launch_bounds__(32 * kTcRedWarps)
 bool tc_supported(const glm_ctx *h)
 {
     return (h->d.xtype == GLM_X_BF16 || h->d.xtype == GLM_X_FP8E4M3) && h->d.p <= kTcMaxP &&
-           h->d.k_max >= 16 && std::getenv("GLM_NO_TC") == nullptr;
+           h->d.k_max >= 16;
 }
 
 // Ring depths that fit: operand-tile stages (2..4) and, for FP8 storage,
-// staged E4M3 half tiles (3, else 2). Returns false if nothing fits.
+// staged E4M3 half tiles (4, else 2: an even count, half the slots for each
+// half tile). Returns false if nothing fits.
 static bool tc_stages(int PA, bool fp8, int *stages, int *raw_stages)
 {
     for (int st = kTcMaxStages; st >= 2; --st) {
-        for (int rs = fp8 ? kTcMaxRawStages : 0; rs >= (fp8 ? 2 : 0); --rs) {
+        for (int rs = fp8 ? kTcMaxRawStages : 0; rs >= (fp8 ? 2 : 0); rs -= 2) {
             if (tc_layout(PA, st, rs).total <= kSmemDynamicBudget) {
                 *stages = st;
                 *raw_stages = rs;
