@@ -30,6 +30,10 @@ Functions and the passages they follow:
   the square-lattice Ising model (§4.3.1) in the natural row-major layout
   (NumPy, FP64); the colour planes only index the uniforms.
 
+``hls_logpost_grad`` is not part of the oracle: it is the multi-core FP64 CPU
+baseline the benchmark times (``cpu_hls.c``, the paper's own CPU design
+restated with OpenMP), checked against ``logpost_grad`` by the tests.
+
 Every function is pinned by ``tests/test_oracle_pins.py`` against closed
 forms, extended-precision brute force, finite differences, symmetries,
 library routines and quadrature.
@@ -61,6 +65,71 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+_HLS_SRC = os.path.join(_HERE, "cpu_hls.c")
+_HLS_PATH = os.path.join(_HERE, "libcpu_hls.so")
+_hls = None
+
+
+def build_hls(force: bool = False) -> str:
+    """Compile cpu_hls.c (the multi-core FP64 CPU baseline) with gcc -fopenmp."""
+    if (not force and os.path.exists(_HLS_PATH)
+            and os.path.getmtime(_HLS_PATH) >= os.path.getmtime(_HLS_SRC)):
+        return _HLS_PATH
+    tmp = _HLS_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", tmp, _HLS_SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _HLS_PATH)
+    return _HLS_PATH
+
+
+def _load_hls():
+    global _hls
+    with _lock:
+        if _hls is not None:
+            return _hls
+        lib = C.CDLL(build_hls())
+        dp = C.POINTER(C.c_double)
+        lib.hls_logpost_grad.argtypes = [dp, C.c_int64, C.c_int32, C.c_int64,
+                                         C.POINTER(C.c_uint8), dp, C.c_int32, C.c_double,
+                                         C.c_int32, dp, dp]
+        lib.hls_logpost_grad.restype = C.c_int
+        lib.hls_max_threads.argtypes = []
+        lib.hls_max_threads.restype = C.c_int
+        _hls = lib
+        return lib
+
+
+def hls_max_threads() -> int:
+    """Processors OpenMP sees on this host."""
+    return int(_load_hls().hls_max_threads())
+
+
+def hls_logpost_grad(X, y, beta, prior_sigma=10.0, p=None, threads=None):
+    """The multi-core CPU baseline (``cpu_hls.c``: the paper's partial loop
+    fusion, cache fusion and one combine per thread, FP64, OpenMP). Same
+    arguments and results as ``logpost_grad``; not the oracle."""
+    Xd = _f64_matrix(X)
+    n, ld = Xd.shape
+    b = np.ascontiguousarray(np.atleast_2d(beta), dtype=np.float64)
+    k, pp = b.shape
+    P = pp if p is None else int(p)
+    if P != pp or P > ld:
+        raise ValueError("beta width must equal P <= ld")
+    yy = np.ascontiguousarray(y, dtype=np.uint8)
+    if yy.shape[0] != n:
+        raise ValueError("y length must equal N")
+    nt = hls_max_threads() if threads is None else int(threads)
+    f = np.empty(k, dtype=np.float64)
+    g = np.empty((k, P), dtype=np.float64)
+    rc = _load_hls().hls_logpost_grad(_p(Xd, C.c_double), n, P, ld, _p(yy, C.c_uint8),
+                                      _p(b, C.c_double), k, float(prior_sigma), nt,
+                                      _p(f, C.c_double), _p(g, C.c_double))
+    if rc != 0:
+        raise ValueError("hls_logpost_grad failed")
+    return f, g
 
 
 def _load():

@@ -18,28 +18,22 @@
 // while X stays in 2-byte storage. Per-CTA partials are combined by a second
 // kernel in a fixed order (deterministic).
 //
-// FP8 E4M3 storage: every E4M3 value is exactly an FP16 normal, so four
-// converter warps turn each staged E4M3 tile into FP16 in the same swizzled
-// layout (one cvt per pair of values) and the MMAs run with FP16 operands;
-// beta and r are split into FP16 hi + lo terms. The column scales fold into
-// the coefficients (eta = q . (s o beta)) and into the final combine
-// (g_j = s_j sum_n q_nj r_n); a power-of-two factor per vector keeps s o beta
-// in FP16 range and is divided out of eta exactly.
+// FP8 E4M3 storage has its own pass (glm_tc8.cu), which takes the E4M3
+// operands directly.
 //
 // Warp roles: warp 0 issues TMA loads, warp 1 allocates tensor memory and one
 // of its threads issues the MMAs, warps 2..17 first load beta into tensor
-// memory and then run the epilogue, and with FP8 storage warps 18..21
-// convert the staged tiles.
+// memory and then run the epilogue.
 // Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
-#include <cuda_fp8.h>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 
 #include "glm_internal.cuh"
+#include "glm_tc_common.cuh"
 
 namespace glm {
 
@@ -49,11 +43,7 @@ constexpr int kTcEpiGroups = kTcEpiWarps / 4;       // warps per tensor-memory l
 constexpr int kTcEpiCols = 128 / kTcEpiGroups;      // D1 columns (tile rows) per warp
 constexpr int kTcEpiRows = kTcEpiCols / 2;          // rows per thread
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
-constexpr int kTcConvWarps = 4;                     // FP8 tile converters
-constexpr int kTcThreadsFp8 = kTcThreads + 32 * kTcConvWarps;
 constexpr int kTcMaxStages = 4;
-constexpr int kTcRawRows = 64;                      // rows per staged E4M3 slot (half a tile)
-constexpr int kTcMaxRawStages = 4;                  // even: RS/2 slots per half tile
 constexpr int kTcMaxP = 256;
 constexpr int kTcMaxKB = 64;
 constexpr int kTcTmemCols = 512;
@@ -67,8 +57,6 @@ struct TcParams {
     int PA;                     // 64-column atoms of the tile
     int MB;                     // 128-column blocks of P for MMA2
     int stages;
-    int raw_stages;             // FP8 storage: staged E4M3 half tiles (64 rows)
-    const float *x_scale;       // FP8 storage: P column scales
     int y_al4;                  // y is 4-byte aligned: labels read as words
     double *part_f;             // grid x 64
     float *part_g;              // grid x 64 x (MB*128)
@@ -84,142 +72,12 @@ __device__ __forceinline__ uint32_t sw128(int r, int c_elem16)
     return (uint32_t)r * 128u + ((chunk ^ ((uint32_t)r & 7u)) << 4) + (((uint32_t)c_elem16 & 7u) << 1);
 }
 
-__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= 1ull << 46;            // descriptor version for tcgen05
-    d |= 2ull << 61;            // 128-byte swizzle
-    return d;
-}
-
 // kind::f16 instruction descriptor: D f32, A and B both bf16 (ab_type 1) or
 // both f16 (ab_type 0), M=128, N=n.
 __host__ __device__ constexpr uint32_t idesc_f16kind(int n, int a_mn, int b_mn, uint32_t ab_type)
 {
     return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)a_mn << 15) |
            ((uint32_t)b_mn << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                    uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     ptx::smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3}], [%4];" ::"r"(ptx::smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(ptx::smem_u32(bar))
-        : "memory");
-}
-
-// 32 lanes x N columns of 32-bit values from tensor memory (N = 8, 16 or 32).
-template <int N>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, float *v);
-
-template <>
-__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float *v)
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        v[i] = __uint_as_float(r[i]);
-}
-
-template <>
-__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float *v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-        v[i] = __uint_as_float(r[i]);
-}
-
-template <>
-__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float *v)
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-        v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r)
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
-        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
-        "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// MMA with the A operand in tensor memory.
-__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
-                                       uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float lg2_approx(float x)
-{
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
 }
 
 // TR map on the hardware base-2 exponential and logarithm, overflow-free:
@@ -271,15 +129,6 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
         return pack_bf16(a, b);
 }
 
-// Four E4M3 codes (one 32-bit word) to four FP16 values (two 32-bit words),
-// exactly: E4M3 values are all FP16 normals or zero.
-__device__ __forceinline__ void e4m3x4_to_f16(uint32_t w, uint32_t &lo, uint32_t &hi)
-{
-    asm("{\n\t.reg .b16 a, b;\n\tmov.b32 {a, b}, %2;\n\t"
-        "cvt.rn.f16x2.e4m3x2 %0, a;\n\tcvt.rn.f16x2.e4m3x2 %1, b;\n\t}"
-        : "=r"(lo), "=r"(hi)
-        : "r"(w));
-}
 
 }  // namespace tc
 
@@ -288,22 +137,18 @@ struct TcLayout {
     int x_stage;    // PA * 16 KB (bf16 / f16 operand tile, 128B swizzle)
     int x_off;
     int r_off;      // R tile: 2 regions of (128 rows x 128 B)
-    int raw_stage;  // FP8 storage: 64 rows x (PA * 64 + 16) bytes
-    int raw_off;
     int bar_off;    // barriers, tensor-memory slot, per-vector scales
     int sf_off;     // 4 x 64 doubles (inside the R tile, used after the last MMA)
     int total;      // including 1 KB alignment slack
 };
 
-__host__ __device__ inline TcLayout tc_layout(int PA, int stages, int raw_stages)
+__host__ __device__ inline TcLayout tc_layout(int PA, int stages)
 {
     TcLayout L;
     L.x_stage = PA * 16384;
     L.x_off = 0;
     L.r_off = stages * L.x_stage;
-    L.raw_stage = raw_stages > 0 ? (kTcRawRows * (PA * 64 + 16) + 1023) / 1024 * 1024 : 0;
-    L.raw_off = L.r_off + 2 * 16384;
-    L.bar_off = L.raw_off + raw_stages * L.raw_stage;
+    L.bar_off = L.r_off + 2 * 16384;
     L.sf_off = L.r_off;
     L.total = L.bar_off + 512 + 1024;
     return L;
@@ -315,12 +160,11 @@ constexpr int kTcB1Col = 0;
 constexpr int kTcD1Col = 128;
 constexpr int kTcD2Col = 256;
 
-template <bool FP8>
-__global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     tc_logpost_grad_kernel(const __grid_constant__ CUtensorMap tmap, TcParams p)
 {
-    // operands: bf16 for BF16 storage, f16 for FP8 storage (A and B alike)
-    constexpr uint32_t AB = FP8 ? 0u : 1u;
+    constexpr bool FP8 = false;     // BF16 operands (kind::f16, ab_type 1)
+    constexpr uint32_t AB = 1u;
     constexpr uint32_t ID1 = tc::idesc_f16kind(128, 0, 0, AB);
     constexpr uint32_t ID2 = tc::idesc_f16kind(128, 1, 1, AB);
 
@@ -329,11 +173,9 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
     const int PA = p.PA;
     const int MB = p.MB;
     const int stages = p.stages;
-    const int RS = p.raw_stages;
-    const TcLayout L = tc_layout(PA, stages, FP8 ? RS : 0);
+    const TcLayout L = tc_layout(PA, stages);
     uint8_t *xs = smem + L.x_off;
     uint8_t *rb = smem + L.r_off;
-    uint8_t *raw = smem + L.raw_off;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bar_off);
     uint64_t *x_full = bars;                    // [stages]
     uint64_t *x_empty = bars + kTcMaxStages;    // [stages]
@@ -342,10 +184,7 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
     uint64_t *r_full = d1_empty + 1;
     uint64_t *r_empty = r_full + 1;
     uint64_t *d2_done = r_empty + 1;
-    uint64_t *raw_full = d2_done + 1;           // [kTcMaxRawStages]
-    uint64_t *raw_empty = raw_full + kTcMaxRawStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw_empty + kTcMaxRawStages);
-    float *vscale = reinterpret_cast<float *>(smem + L.bar_off + 256);   // [64]: 2^-e_k
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d2_done + 1);
     double *sf = reinterpret_cast<double *>(smem + L.sf_off);
     __shared__ int s_abort;
 
@@ -356,16 +195,11 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
     const int b = blockIdx.x;
     const int64_t ntiles_all = (p.N + kTcRows - 1) / kTcRows;
     const int nt = (int)(ntiles_all > b ? (ntiles_all - b + grid - 1) / grid : 0);
-    const int raw_row = PA * 64 + 16;           // staged E4M3 row: one zero chunk wider
 
     if (tid == 0) {
         for (int s = 0; s < kTcMaxStages; ++s) {
-            ptx::mbar_init(&x_full[s], FP8 ? kTcConvWarps : 1);
+            ptx::mbar_init(&x_full[s], 1);
             ptx::mbar_init(&x_empty[s], 1);
-        }
-        for (int s = 0; s < kTcMaxRawStages; ++s) {
-            ptx::mbar_init(&raw_full[s], 1);
-            ptx::mbar_init(&raw_empty[s], kTcConvWarps / 2);   // the warps of one half tile
         }
         ptx::mbar_init(d1_full, 1);
         ptx::mbar_init(d1_empty, kTcEpiWarps);
@@ -394,29 +228,11 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
     // storage: the coefficients are s_j beta_kj times 2^e_k, with e_k the
     // power of two that brings max_j |s_j beta_kj| just under 2^14.
     constexpr int EPI0 = 2;                         // first epilogue warp
-    constexpr int CONV0 = 2 + kTcEpiWarps;          // first converter warp (FP8)
     if (warp >= EPI0 && warp < EPI0 + 4) {
         const int q = warp & 3;
         const int n = q * 32 + lane;
         const int k = n >> 1;
         const int part = n & 1;
-        float scale = 1.0f;
-        if constexpr (FP8) {
-            float m = 0.0f;
-            if (k < p.kk)
-                for (int col = 0; col < p.P; ++col)
-                    m = fmaxf(m, fabsf(p.beta[(size_t)k * p.P + col] * p.x_scale[col]));
-            int e = 0;
-            if (m > 0.0f) {
-                int ex;
-                frexpf(m, &ex);                 // m < 2^ex
-                e = 14 - ex;
-                e = e < -100 ? -100 : (e > 100 ? 100 : e);
-            }
-            scale = ldexpf(1.0f, e);
-            if (part == 0 && k < 64)
-                vscale[k] = ldexpf(1.0f, -e);
-        }
         for (int cb = 0; cb < PA * 32; cb += 32) {
             uint32_t r[32];
 #pragma unroll
@@ -426,11 +242,8 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                 for (int e = 0; e < 2; ++e) {
                     const int col = 2 * (cb + j) + e;
                     float v = 0.0f;
-                    if (k < p.kk && col < p.P) {
+                    if (k < p.kk && col < p.P)
                         v = p.beta[(size_t)k * p.P + col];
-                        if constexpr (FP8)
-                            v = v * p.x_scale[col] * scale;
-                    }
                     float hi, lo;
                     tc::split2<FP8>(v, hi, lo);
                     v2[e] = part ? lo : hi;
@@ -449,40 +262,19 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
       if (warp == 0) {
         // ---- TMA producer ------------------------------------------------------------
         if (lane == 0) {
-            if constexpr (!FP8) {
-                const unsigned bytes = (unsigned)(PA * 16384);
-                for (int i = 0; i < nt; ++i) {
-                    const int s = i % stages;
-                    const int use = i / stages;
-                    if (use > 0 && !ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
-                        atomicOr(p.status, kDevTimeout);
-                        s_abort = 1;
-                        break;
-                    }
-                    const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kTcRows);
-                    ptx::mbar_arrive_expect_tx(&x_full[s], bytes);
-                    for (int a = 0; a < PA; ++a)
-                        tc::tma_load_2d(xs + s * L.x_stage + a * 16384, &tmap, a * 64, row0, &x_full[s]);
+            const unsigned bytes = (unsigned)(PA * 16384);
+            for (int i = 0; i < nt; ++i) {
+                const int s = i % stages;
+                const int use = i / stages;
+                if (use > 0 && !ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
+                    atomicOr(p.status, kDevTimeout);
+                    s_abort = 1;
+                    break;
                 }
-            } else {
-                // E4M3 half tiles (64 rows) into the raw ring, each row one chunk
-                // wider than stored (the extra chunk is outside the tensor: zero fill)
-                const unsigned bytes = (unsigned)(kTcRawRows * raw_row);
-                for (int u = 0; u < 2 * nt; ++u) {
-                    // each half tile has its own RS/2 slots, so every waiter
-                    // on a slot has consumed that slot's previous use
-                    const int s = (u & 1) + 2 * ((u >> 1) % (RS / 2));
-                    const int use = (u >> 1) / (RS / 2);
-                    if (use > 0 && !ptx::mbar_wait_bounded(&raw_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
-                        atomicOr(p.status, kDevTimeout);
-                        s_abort = 1;
-                        break;
-                    }
-                    const int row0 = (int)((int64_t)(b + (int64_t)(u >> 1) * grid) * kTcRows) +
-                                     (u & 1) * kTcRawRows;
-                    ptx::mbar_arrive_expect_tx(&raw_full[s], bytes);
-                    tc::tma_load_2d(raw + s * L.raw_stage, &tmap, 0, row0, &raw_full[s]);
-                }
+                const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kTcRows);
+                ptx::mbar_arrive_expect_tx(&x_full[s], bytes);
+                for (int a = 0; a < PA; ++a)
+                    tc::tma_load_2d(xs + s * L.x_stage + a * 16384, &tmap, a * 64, row0, &x_full[s]);
             }
         }
       } else if (warp == 1) {
@@ -545,63 +337,6 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                 tc::commit(d2_done);
         }
       }
-    } else if (FP8 && warp >= CONV0) {
-        // ---- E4M3 -> FP16 converters ----------------------------------------------------
-        // thread ct takes tile row ct (warps 0-1 the first half tile, 2-3 the
-        // second): reads 16-byte chunks of its staged row (odd chunk stride:
-        // 8 consecutive rows hit distinct bank groups) and writes two 16-byte
-        // FP16 chunks per E4M3 chunk into the 128B-swizzled operand tile
-        const int ct = (warp - CONV0) * 32 + lane;
-        const int half = ct / kTcRawRows;
-        const int r = ct;
-        const uint32_t rx = (uint32_t)(r & 7);
-        bool ok = true;
-        for (int i = 0; i < nt; ++i) {
-            const int rs = half + 2 * (i % (RS / 2));
-            const int s = i % stages;
-            ok = ptx::mbar_wait_bounded(&raw_full[rs], (unsigned)(i / (RS / 2)) & 1u, kSpinLimit);
-            if (ok && i >= stages)
-                ok = ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(i / stages - 1) & 1u, kSpinLimit);
-            if (!ok)
-                break;
-            const uint8_t *src = raw + rs * L.raw_stage + (r - half * kTcRawRows) * raw_row;
-            uint8_t *dst_r = xs + s * L.x_stage + r * 128;
-            // eight 16-byte loads in flight before converting (PA * 4 chunks
-            // per row, a multiple of 4: the tail group is guarded)
-            for (int c0 = 0; c0 < PA * 4; c0 += 8) {
-                uint4 a[8];
-#pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    if (c0 + v < PA * 4)
-                        a[v] = *reinterpret_cast<const uint4 *>(src + (c0 + v) * 16);
-#pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const int c = c0 + v;
-                    if (c < PA * 4) {
-                        uint4 o0, o1;
-                        tc::e4m3x4_to_f16(a[v].x, o0.x, o0.y);
-                        tc::e4m3x4_to_f16(a[v].y, o0.z, o0.w);
-                        tc::e4m3x4_to_f16(a[v].z, o1.x, o1.y);
-                        tc::e4m3x4_to_f16(a[v].w, o1.z, o1.w);
-                        // FP16 columns 16c .. 16c + 15: atom c / 4, chunks 2 (c % 4) and +1
-                        uint8_t *atom = dst_r + (c >> 2) * 16384;
-                        const uint32_t ch = (uint32_t)((c & 3) * 2);
-                        *reinterpret_cast<uint4 *>(atom + ((ch ^ rx) << 4)) = o0;
-                        *reinterpret_cast<uint4 *>(atom + (((ch + 1) ^ rx) << 4)) = o1;
-                    }
-                }
-            }
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                ptx::mbar_arrive(&raw_empty[rs]);
-                ptx::mbar_arrive(&x_full[s]);
-            }
-        }
-        if (!ok) {
-            atomicOr(p.status, kDevTimeout);
-            s_abort = 1;
-        }
     } else {
         // ---- epilogue ---------------------------------------------------------------------
         constexpr int CW = kTcEpiCols;
@@ -617,9 +352,6 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
         // j): its R-tile stores then fall in other 16-byte chunks of the
         // swizzle than the hi lane's, and the two halves do not conflict
         const int rot = part ? 4 : 0;
-        float vs = 1.0f;                        // 2^-e_k (FP8 storage)
-        if constexpr (FP8)
-            vs = vscale[k];
         float facc = 0.0f;
         uint32_t yw[RT / 4], yn[RT / 4];
         auto load_y = [&](int i, uint32_t *dst) {
@@ -679,8 +411,6 @@ __global__ void __launch_bounds__(FP8 ? kTcThreadsFp8 : kTcThreads, 1)
                 const int pj = (j + 4) & (RT - 1);
                 const float send = part ? v[j] : v[RT + pj];
                 mine[j] = (part ? v[RT + pj] : v[j]) + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
-                if constexpr (FP8)
-                    mine[j] *= vs;
             }
             if (nvalid == RT) {
 #pragma unroll
@@ -865,26 +595,20 @@ bool tc_supported(const glm_ctx *h)
            h->d.k_max >= 16;
 }
 
-// Ring depths that fit: operand-tile stages (2..4) and, for FP8 storage,
-// staged E4M3 half tiles (4, else 2: an even count, half the slots for each
-// half tile). Returns false if nothing fits.
-static bool tc_stages(int PA, bool fp8, int *stages, int *raw_stages)
+// Operand-tile stages that fit (4 down to 2). Returns false if nothing fits.
+static bool tc_stages(int PA, int *stages)
 {
     for (int st = kTcMaxStages; st >= 2; --st) {
-        for (int rs = fp8 ? kTcMaxRawStages : 0; rs >= (fp8 ? 2 : 0); rs -= 2) {
-            if (tc_layout(PA, st, rs).total <= kSmemDynamicBudget) {
-                *stages = st;
-                *raw_stages = rs;
-                return true;
-            }
+        if (tc_layout(PA, st).total <= kSmemDynamicBudget) {
+            *stages = st;
+            return true;
         }
     }
     return false;
 }
 
 // BF16: 64-column boxes with the 128B swizzle, loaded straight into the MMA
-// layout. FP8: the E4M3 rows as 16-bit pairs in one box one chunk wider
-// than the padded row (the extra chunk is outside the tensor: zero fill).
+// layout.
 static glm_status_t tc_tensor_map(glm_ctx *h, const void *X)
 {
     if (h->tc_map_ptr == X)
@@ -895,22 +619,12 @@ static glm_status_t tc_tensor_map(glm_ctx *h, const void *X)
     CUtensorMap *map = reinterpret_cast<CUtensorMap *>(h->tc_map);
     const cuuint32_t estr[2] = {1, 1};
     CUresult r;
-    if (h->d.xtype == GLM_X_FP8E4M3) {
-        const int PA = (h->d.p + 63) / 64;
-        const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld / 2, (cuuint64_t)h->d.n_rows};
-        const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld};
-        const cuuint32_t box[2] = {(cuuint32_t)(PA * 32 + 8), (cuuint32_t)kTcRawRows};
-        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(X), dims, strides, box,
-                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    } else {
-        const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld, (cuuint64_t)h->d.n_rows};
-        const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld * 2};
-        const cuuint32_t box[2] = {64, (cuuint32_t)kTcRows};
-        r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(X), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    }
+    const cuuint64_t dims[2] = {(cuuint64_t)h->d.ld, (cuuint64_t)h->d.n_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)h->d.ld * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)kTcRows};
+    r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(X), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return GLM_ERR_CUDA;
     h->tc_map_ptr = X;
@@ -923,9 +637,14 @@ size_t tc_workspace_bytes(const glm_ctx *h)
     return (size_t)h->sm_count * kTcMaxKB * 8 + (size_t)h->sm_count * kTcMaxKB * MB * 128 * 4 + 256;
 }
 
+glm_status_t launch_tc8(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
+                        const float *beta, int K, double *f_out, float *g_out, cudaStream_t s);
+
 glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const uint8_t *y,
                        const float *beta, int K, double *f_out, float *g_out, cudaStream_t s)
 {
+    if (h->d.xtype == GLM_X_FP8E4M3)
+        return launch_tc8(h, X, x_scale, y, beta, K, f_out, g_out, s);
     if (!h->tc_part_f || h->d.n_rows > ((int64_t)1 << 31) - kTcRows)
         return GLM_ERR_UNSUPPORTED;
     glm_status_t st = tc_tensor_map(h, X);
@@ -937,9 +656,8 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
     const double s2 = h->d.prior_sigma * h->d.prior_sigma;
     const bool prior = !(h->d.flags & GLM_FLAG_NO_PRIOR);
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(h->tc_map);
-    const bool fp8 = h->d.xtype == GLM_X_FP8E4M3;
-    int stages = 0, raw_stages = 0;
-    if (!tc_stages(PA, fp8, &stages, &raw_stages))
+    int stages = 0;
+    if (!tc_stages(PA, &stages))
         return GLM_ERR_UNSUPPORTED;
     for (int k0 = 0; k0 < K; k0 += kTcMaxKB) {
         const int kk = (K - k0) < kTcMaxKB ? (K - k0) : kTcMaxKB;
@@ -955,18 +673,16 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         prm.PA = PA;
         prm.MB = MB;
         prm.stages = stages;
-        prm.raw_stages = raw_stages;
-        prm.x_scale = x_scale;
         prm.part_f = h->tc_part_f;
         prm.part_g = h->tc_part_g;
         prm.status = h->status;
-        auto fn = fp8 ? &tc_logpost_grad_kernel<true> : &tc_logpost_grad_kernel<false>;
-        const TcLayout L = tc_layout(PA, prm.stages, prm.raw_stages);
+        auto fn = &tc_logpost_grad_kernel;
+        const TcLayout L = tc_layout(PA, prm.stages);
         if (allow_max_dynamic_smem(reinterpret_cast<const void *>(fn)) != cudaSuccess)
             return GLM_ERR_CUDA;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)h->sm_count);
-        cfg.blockDim = dim3(fp8 ? kTcThreadsFp8 : kTcThreads);
+        cfg.blockDim = dim3(kTcThreads);
         cfg.dynamicSmemBytes = (size_t)L.total;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
