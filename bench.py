@@ -77,6 +77,7 @@ GROUPED_SOURCES = ["paper_1310_1537_gb300/csrc/glm_grouped.cu",
 SLICE_SOURCES = ["paper_1310_1537_gb300/csrc/glm_slice.cu",
                  "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 HESS_SOURCES = ["paper_1310_1537_gb300/csrc/glm_hess.cu",
+                "paper_1310_1537_gb300/csrc/glm_tc_common.cuh",
                 "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
 ISING_SOURCES = ["paper_1310_1537_gb300/csrc/glm_ising.cu",
                  "paper_1310_1537_gb300/csrc/glm_internal.cuh"]
@@ -98,6 +99,16 @@ def algorithmic_bytes_per_step(n=N_ROWS, p=P, ld=P, es=4) -> int:
     ins = 2 * p * 4 + 8 + 8          # state, z, f_state, log u
     outs = 8 + p * 4 + p * 4 + 1 + 8 + 8  # f, g, sample, accept, logpost, f_state
     return x + y + ins + outs
+
+
+def measured_bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 def measured_hbm_peak():
@@ -1121,7 +1132,7 @@ def run_ising(args, local):
 
 def run_hessian(args, local):
     """One pass returning f, g and the Hessian (N = 2,000,000, P = 64, FP32,
-    one coefficient vector). CUDA-core FP32 arithmetic bound."""
+    one coefficient vector); X^T W X on the tensor cores."""
     import torch
     import synth
     import paper_1310_1537_gb300 as glm
@@ -1179,22 +1190,31 @@ def run_hessian(args, local):
         oracle.logpost_grad_hess(X64, d.y[:rows], b64)
         k += 1
     cpu = 1.0 / ((time.perf_counter() - t1) / k * n / rows)
-    flops = n * (2 * p + 2 * p + p * (p + 1))     # eta, g, upper triangle of X^T W X
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12           # FP32 FMA lanes x 2 FLOP x max SM clock
-    achieved = flops / (ms / 1e3) / 1e12
-    return ({
+    flops = 2 * n * p * p                          # X^T W X (the full P x P contraction)
+    # issued tensor-core work: per 128-row tile one 128 x 128 x 128 product
+    # (hi/lo terms of w x against hi/lo terms of x), BF16 operands
+    mma_flops = 2 * 128 * 128 * 128 * (-(-n // 128))
+    bf16_peak = measured_bf16_peak()
+    bytes_eval = n * p * 4 + n + p * 4 + 8 + p * 4 + p * p * 4
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bytes_eval / (ms / 1e3) / 1e9
+    line = ({
         "metric": "log-posterior+grad+Hessian evals/s", "value": 1e3 / ms, "unit": "evals/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"one-pass f, g, Hessian: N={n}, P={p}, X FP32 row-major, K=1",
-                   "l2": "inputs larger than L2 (X 512 MB), no flush",
-                   "hbm_bytes_per_eval": n * p * 4 + n},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                   "path": "tcgen05 kind::f16: X^T W X from BF16 hi/lo terms, D in tensor memory",
+                   "l2": "inputs larger than L2 (X 512 MB), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": profile_traffic(os.path.join(ROOT, "profiles", "hess_big.md"),
                                                 HESS_SOURCES),
-                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": bytes_eval,
+                     "tensor_tflops_issued": mma_flops / (ms / 1e3) / 1e12,
+                     "tensor_frac": mma_flops / (ms / 1e3) / 1e12 / bf16_peak[0],
+                     "tensor_peak_kind": f"{bf16_peak[1]} bf16_tflops (dense, burst)",
                      "algorithmic_flops_per_eval": flops},
         "cpu_baseline": {"value": cpu, "unit": "evals/s", "cores": 1, "kind": "oracle",
                          "sample": f"{k} NumPy evaluations on rows [0, {rows}), scaled to N={n}"},
@@ -1203,6 +1223,7 @@ def run_hessian(args, local):
                 "api": "glm_hess_eval with beta in and f, g, H out, synced"},
         "clocks": clocks, "gpu_launches": 2 * args.steps,
     })
+    return line
 
 
 SERVING_RATE = 2000.0
