@@ -35,7 +35,9 @@ parts of the path, each printing its own JSON line:
 - ``serving``: Poisson arrivals at 2,000 requests/s (``--rate``; 0 submits all at once) against 16 resident BF16
   datasets (N log-uniform in [1e3, 4e6], P log-uniform in [8, 512]), K
   uniform in 1..32 per request; one step is one request. Reports latency
-  percentiles from submission to results on the host.
+  percentiles from submission to results on the host, the pass that served
+  each batch, the device memory account, and a second stream at 20,000
+  requests/s (``--overlap-rate``) where arrivals overlap and batches merge.
 """
 from __future__ import annotations
 
@@ -579,7 +581,8 @@ def run_workload_suite(args, local, d_big):
          ("fp32_k64_loop", "path")),
         ("grouped", lambda: run_grouped(sub(20, 5, 3.0), local), ()),
         ("serving", lambda: run_serving(sub(2000, 100, 2.5, rate=SERVING_RATE), local),
-         ("latency_ms", "requests_per_s", "batching", "accuracy_vs_oracle", "admission")),
+         ("latency_ms", "requests_per_s", "batching", "accuracy_vs_oracle", "admission",
+          "overlap_stream")),
         ("slice", lambda: run_slice(sub(2, 1, 3.0, spec=0), local, d_big),
          ("passes_per_update", "us_per_pass")),
         ("ising", lambda: run_ising(sub(10, 3, 3.0), local), ()),
@@ -1253,55 +1256,88 @@ def run_serving(args, local):
         ds = glm.glm_server_add_dataset(server, Xq, None, yd, n, p, ld, glm.GLM_X_BF16,
                                         PRIOR_SIGMA)
         dsets.append(dict(n=n, p=p, ld=ld, Xq=Xq, y=yd, d=d, id=ds))
-    count = args.warmup + args.steps
-    rng = np.random.default_rng(seed + 100)
-    reqs = []
-    for _ in range(count):
-        i = int(rng.integers(len(dsets)))
-        k = int(rng.integers(1, 33))
-        it = dsets[i]
-        b = (it["d"].beta_star[None, :] + 0.05 * rng.standard_normal((k, it["p"])))
-        reqs.append((i, k, np.ascontiguousarray(b, dtype=np.float32)))
-    rate = SERVING_RATE if args.rate is None else args.rate
-    arrivals = (synth.poisson_arrivals(rate, count, seed + 101) if rate > 0
-                else np.zeros(count))
-    rids = [0] * count
-    submit_lag = np.zeros(count)
-    ready = threading.Semaphore(0)
+    def stream(rate, count, seed_off, keep_from, keep_every):
+        """One request stream at `rate` requests/s (0: all at once); returns
+        the request infos, kept results, failures, submit lags and requests."""
+        rng = np.random.default_rng(seed + seed_off)
+        reqs = []
+        for _ in range(count):
+            i = int(rng.integers(len(dsets)))
+            k = int(rng.integers(1, 33))
+            it = dsets[i]
+            b = (it["d"].beta_star[None, :] + 0.05 * rng.standard_normal((k, it["p"])))
+            reqs.append((i, k, np.ascontiguousarray(b, dtype=np.float32)))
+        arrivals = (synth.poisson_arrivals(rate, count, seed + seed_off + 1) if rate > 0
+                    else np.zeros(count))
+        rids = [0] * count
+        submit_lag = np.zeros(count)
+        ready = threading.Semaphore(0)
 
-    def submitter():
-        t0 = time.perf_counter()
+        def submitter():
+            t0 = time.perf_counter()
+            for j, (i, k, b) in enumerate(reqs):
+                while True:
+                    rem = arrivals[j] - (time.perf_counter() - t0)
+                    if rem <= 0:
+                        break
+                    if rem > 4e-4:
+                        time.sleep(rem - 3e-4)
+                submit_lag[j] = time.perf_counter() - t0 - arrivals[j]
+                rids[j] = glm.glm_server_submit(server, dsets[i]["id"], b, k)
+                ready.release()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        infos, outs, failures = [], {}, []
+        keep = set(range(keep_from, count, keep_every))
         for j, (i, k, b) in enumerate(reqs):
-            while True:
-                rem = arrivals[j] - (time.perf_counter() - t0)
-                if rem <= 0:
-                    break
-                if rem > 4e-4:
-                    time.sleep(rem - 3e-4)
-            submit_lag[j] = time.perf_counter() - t0 - arrivals[j]
-            rids[j] = glm.glm_server_submit(server, dsets[i]["id"], b, k)
-            ready.release()
+            ready.acquire()
+            fbuf = np.empty(k, np.float64)
+            gbuf = np.empty((k, b.shape[1]), np.float32)
+            try:
+                infos.append(glm.glm_server_wait(server, rids[j], fbuf, gbuf, timeout_ms=120000))
+            except glm.GLMError as e:
+                failures.append({"request": j, "dataset": i, "n": dsets[i]["n"],
+                                 "p": dsets[i]["p"], "k": k, "status": e.status})
+                continue
+            if j in keep:
+                outs[j] = (fbuf, gbuf)
+        th.join()
+        return infos, outs, failures, submit_lag, reqs
 
+    def batch_table(timed):
+        batches = {}
+        for r in timed:
+            batches.setdefault((r["start_ns"], r["batch_k"]), (r["batch_requests"], r["path"]))
+        return batches
+
+    rate = SERVING_RATE if args.rate is None else args.rate
+    count = args.warmup + args.steps
     sampler = _gpu_sampler(local)
     sampler.start()
-    th = threading.Thread(target=submitter)
-    th.start()
-    infos, outs, failures = [], {}, []
-    keep = set(range(args.warmup, count, max(1, args.steps // 400)))
-    for j, (i, k, b) in enumerate(reqs):
-        ready.acquire()
-        fbuf = np.empty(k, np.float64)
-        gbuf = np.empty((k, b.shape[1]), np.float32)
-        try:
-            infos.append(glm.glm_server_wait(server, rids[j], fbuf, gbuf, timeout_ms=120000))
-        except glm.GLMError as e:
-            failures.append({"request": j, "dataset": i, "n": dsets[i]["n"], "p": dsets[i]["p"],
-                             "k": k, "status": e.status})
-            continue
-        if j in keep:
-            outs[j] = (fbuf, gbuf)
-    th.join()
+    infos, outs, failures, submit_lag, reqs = stream(rate, count, 100, args.warmup,
+                                                      max(1, args.steps // 400))
     clocks = sampler.stop()
+    # a second stream at a rate where arrivals for one dataset overlap the
+    # batches in flight, so that merging is exercised beyond the saturation case
+    overlap = None
+    if failures == [] and args.overlap_rate > 0 and rate > 0:
+        o_infos, _, o_fail, _, _ = stream(args.overlap_rate, 2 * args.steps + args.warmup, 200,
+                                          1 << 62, 1)
+        failures += o_fail
+        o_timed = o_infos[args.warmup:]
+        o_lat = np.array([(r["done_ns"] - r["submit_ns"]) * 1e-6 for r in o_timed])
+        o_span = (max(r["done_ns"] for r in o_timed) - min(r["submit_ns"] for r in o_timed)) * 1e-9
+        o_batches = batch_table(o_timed)
+        overlap = {"rate_per_s": args.overlap_rate, "requests": len(o_timed),
+                   "value": sum(r["k"] for r in o_timed) / o_span, "unit": UNIT,
+                   "requests_per_s": len(o_timed) / o_span,
+                   "latency_ms": {"p50": float(np.percentile(o_lat, 50)),
+                                  "p99": float(np.percentile(o_lat, 99))},
+                   "mean_requests_per_batch": float(np.mean([v[0] for v in o_batches.values()])),
+                   "mean_vectors_per_batch": float(np.mean([bk for _, bk in o_batches])),
+                   "batches_tensor_cores": sum(1 for v in o_batches.values()
+                                               if v[1] == glm.GLM_PATH_TENSOR_CORES)}
     stats = glm.glm_server_stats(server)
     glm.glm_server_destroy(server)
     if failures:
@@ -1312,9 +1348,7 @@ def run_serving(args, local):
     queue_ms = np.array([(r["start_ns"] - r["submit_ns"]) * 1e-6 for r in timed])
     span_s = (max(r["done_ns"] for r in timed) - min(r["submit_ns"] for r in timed)) * 1e-9
     vectors = sum(r["k"] for r in timed)
-    batches = {}
-    for r in timed:
-        batches.setdefault((r["start_ns"], r["batch_k"]), r["batch_requests"])
+    batches = batch_table(timed)
     # accuracy: sampled requests against the FP64 oracle on the rounded X,
     # bounded to about 20 s of oracle time
     import oracle
@@ -1361,11 +1395,26 @@ def run_serving(args, local):
                        "queue_p99": float(np.percentile(queue_ms, 99)),
                        "def": "host steady clock, request submitted -> results on the host"},
         "submit_lag_ms_p99": float(np.percentile(submit_lag[args.warmup:], 99) * 1e3),
+        "overlap_stream": overlap,
         "requests_per_s": args.steps / span_s,
         "batching": {"batches": len(batches),
-                     "mean_requests_per_batch": float(np.mean(list(batches.values()))),
+                     "mean_requests_per_batch": float(np.mean([v[0] for v in batches.values()])),
+                     "mean_vectors_per_batch": float(np.mean([bk for _, bk in batches])),
+                     "batches_tensor_cores": sum(1 for v in batches.values()
+                                                 if v[1] == glm.GLM_PATH_TENSOR_CORES),
+                     "batches_cuda_cores": sum(1 for v in batches.values()
+                                               if v[1] == glm.GLM_PATH_CUDA_CORES),
+                     "path_rule": "tensor cores for batches of >= 16 vectors on datasets "
+                                  "with P <= 256, else CUDA cores",
                      "max_concurrent_batches": stats["max_concurrent_batches"],
                      "failed": stats["requests_failed"]},
+        "admission": {"budget_bytes": stats["hbm_budget_bytes"],
+                      "resident_bytes": stats["hbm_resident_bytes"],
+                      "deferrals": stats["deferrals"],
+                      "trimmed_batches": stats["trimmed_batches"],
+                      "refused_requests": stats["refused_requests"],
+                      "rule": "datasets + per-slot workspaces + batches in flight within "
+                              "the budget (default: free device memory at start less 1/16)"},
         "accuracy_vs_oracle": {"requests_checked": checked,
                                "max_rel_err_f": max(errs_f) if errs_f else None,
                                "max_rel_err_g": max(errs_g) if errs_g else None,
@@ -1393,6 +1442,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rate", type=float, default=None,
                     help="serving arrival rate in requests/s (0: all at once); default 2000")
+    ap.add_argument("--overlap-rate", type=float, default=20000.0,
+                    help="serving: rate of a second stream where arrivals overlap (0: none)")
     ap.add_argument("--spec", type=int, default=0,
                     help="slice workload: shrinkage proposals per evaluation pass (0: 2)")
     ap.add_argument("--workload", default="big",

@@ -303,21 +303,36 @@ GLM_API glm_status_t glm_logpost_grad_noalloc(const void *X, const float *x_scal
  * f and g of their own coefficient vectors against datasets held resident on
  * one GPU.
  *
- * A server owns a scheduler thread, a pool of `streams` CUDA streams, pinned
- * host staging per stream and one device arena of `hbm_budget_bytes` for the
- * batches in flight (0 = one eighth of the device's free memory, capped at
- * one half). Requests are queued in arrival order. The scheduler takes the
- * oldest waiting request, merges every later waiting request for the same
- * dataset while the merged batch holds at most max_batch_k vectors, and runs
- * the batch on a free stream as soon as the arena has room for its
- * coefficient, f and g buffers (admission by free device memory; a batch
- * that does not fit waits for a completion). Batches for different datasets
- * run concurrently on different streams.
+ * A server owns a scheduler thread, a pool of `streams` CUDA streams and
+ * pinned host staging per stream. Requests are queued in arrival order. The
+ * scheduler takes the oldest waiting request, merges later waiting requests
+ * for the same dataset while the merged batch holds at most max_batch_k
+ * vectors, and runs the batch on a free stream once memory admits it.
+ * Batches for different datasets run concurrently on different streams.
+ *
+ * Device memory admission. The server keeps one account of the device memory
+ * it stands for, against a budget (hbm_budget_bytes; 0 = the device's free
+ * memory when the server is created, less one sixteenth kept back):
+ *  - resident: each registered dataset's X, y and x_scale (the caller's
+ *    memory, counted at its size) plus the evaluation workspaces the server
+ *    creates for it, one per stream slot;
+ *  - in flight: each running batch's coefficient, f and g buffers, taken
+ *    from a stream-ordered pool the server owns and returned when the batch's
+ *    copies are done.
+ * A dataset whose footprint does not fit what the budget leaves, or whose
+ * workspaces the device cannot allocate, is refused (GLM_ERR_OOM, nothing
+ * kept). A request whose batch could not fit even with nothing in flight is
+ * refused at submit (GLM_ERR_OOM). Otherwise a batch that does not fit now
+ * is first trimmed to the requests that do (the oldest always stays in it)
+ * and, when even the oldest does not fit, deferred until a running batch
+ * completes; the same holds when the pool cannot get the memory from the
+ * device. Deferred requests keep their place in the queue.
  *
  * Each vector's result is the one glm_logpost_grad gives for it in a batch
- * of that batch's size: batches of 16 or more BF16 vectors take the
- * tensor-core path, smaller ones the CUDA-core path, so a result alone and
- * inside a mix agree to the evaluation tolerance.
+ * of that batch's size: batches of 16 or more BF16 or FP8 vectors take the
+ * tensor-core pass where the shape allows it (p <= 256), the others the
+ * CUDA-core pass, so a result alone and inside a mix agree to the evaluation
+ * tolerance. Each request reports the pass that served its batch.
  * ---------------------------------------------------------------------- */
 typedef struct glm_server *glm_server_t;
 
@@ -326,8 +341,15 @@ typedef struct {
     int32_t streams;           /* stream slots, 1..16                          */
     int32_t max_batch_k;       /* largest merged batch in vectors, 1..1024     */
     int32_t max_pending;       /* queue limit; submit past it returns OOM      */
-    int64_t hbm_budget_bytes;  /* arena for batches in flight (0 = default)    */
+    int64_t hbm_budget_bytes;  /* device memory account (0 = default, above)   */
 } glm_server_desc_t;
+
+/* The evaluation pass that served a batch (glm_request_info_t.path). */
+typedef enum {
+    GLM_PATH_NONE = 0,             /* not run (failed before the evaluation)  */
+    GLM_PATH_CUDA_CORES = 1,       /* fused CUDA-core pass                    */
+    GLM_PATH_TENSOR_CORES = 2      /* tcgen05 pass (BF16 or FP8 operands)     */
+} glm_path_t;
 
 typedef struct {
     int64_t submit_ns;         /* steady-clock times of the request's life     */
@@ -337,6 +359,8 @@ typedef struct {
     int32_t batch_requests;    /* requests merged into that batch              */
     int32_t k;                 /* this request's vectors                       */
     int32_t status;            /* glm_status_t of the request                  */
+    int32_t path;              /* glm_path_t of the batch that carried it      */
+    int32_t deferrals;         /* times its batch was deferred for memory      */
 } glm_request_info_t;
 
 typedef struct {
@@ -347,6 +371,11 @@ typedef struct {
     int64_t vectors_done;
     int64_t hbm_budget_bytes;
     int64_t hbm_in_flight_bytes;
+    int64_t hbm_resident_bytes;   /* registered datasets and their workspaces   */
+    int64_t batches_tensor_cores; /* batches served by the tensor-core pass     */
+    int64_t deferrals;            /* dispatches deferred for memory             */
+    int64_t trimmed_batches;      /* batches cut short to fit the budget        */
+    int64_t refused_requests;     /* submits refused: batch can never fit       */
     int32_t max_concurrent_batches;
     int32_t last_cuda_error;   /* cudaError_t of the last failed step (0: none) */
     int32_t last_error_site;   /* glm_server_error_site_t of that step          */
@@ -363,22 +392,33 @@ typedef enum {
 } glm_server_error_site_t;
 
 /* Create a server on desc->device. Returns GLM_ERR_NO_DEVICE without a GPU,
- * GLM_ERR_INVALID_ARG on a bad descriptor, GLM_ERR_OOM if the arena cannot
- * be allocated. */
+ * GLM_ERR_INVALID_ARG on a bad descriptor, GLM_ERR_OOM if the budget is
+ * below 64 KB or the batch memory pool or staging cannot be created. */
 GLM_API glm_status_t glm_server_create(const glm_server_desc_t *desc, glm_server_t *out);
 
 /* Register a device-resident dataset (same layout and storage types as the
  * handle API: X row-major n_rows x ld, y n_rows bytes, x_scale for FP8). The
- * caller keeps X, x_scale and y alive and unchanged until glm_server_destroy.
- * Creates one evaluation handle per stream slot. Returns the dataset's id. */
+ * caller keeps X, x_scale and y alive and unchanged until the dataset is
+ * removed or the server destroyed. Creates one evaluation handle per stream
+ * slot. Returns the dataset's id, or GLM_ERR_OOM (nothing registered) when
+ * the dataset's footprint does not fit the budget that is left or the
+ * device cannot allocate its workspaces. */
 GLM_API glm_status_t glm_server_add_dataset(glm_server_t s, const void *X, const float *x_scale,
                                             const uint8_t *y, int64_t n_rows, int32_t p,
                                             int32_t ld, int32_t xtype, double prior_sigma,
                                             int32_t *dataset_id);
 
+/* Unregister a dataset: GLM_PENDING (nothing changed) while requests for it
+ * are waiting or running, else its workspaces are freed, its footprint leaves
+ * the account and later submits for it return GLM_ERR_INVALID_ARG. The
+ * caller may free X, x_scale and y once this returns GLM_OK. */
+GLM_API glm_status_t glm_server_remove_dataset(glm_server_t s, int32_t dataset_id);
+
 /* Queue a request: K (1..max_batch_k) FP32 vectors beta_host[K x P] in HOST
  * memory, copied before the call returns. Returns a request id, or
- * GLM_ERR_OOM when max_pending requests are already waiting. Thread-safe. */
+ * GLM_ERR_OOM when max_pending requests are already waiting or when a batch
+ * of K vectors for this dataset could not fit the budget even with nothing
+ * in flight. Thread-safe. */
 GLM_API glm_status_t glm_server_submit(glm_server_t s, int32_t dataset_id, const float *beta_host,
                                        int32_t K, uint64_t *request_id);
 

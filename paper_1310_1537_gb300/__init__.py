@@ -28,6 +28,10 @@ GLM_X_F32 = 0
 GLM_X_BF16 = 1
 GLM_X_FP8E4M3 = 2
 
+GLM_PATH_NONE = 0
+GLM_PATH_CUDA_CORES = 1
+GLM_PATH_TENSOR_CORES = 2
+
 GLM_FLAG_NO_TENSOR_CORES = 0x1
 GLM_FLAG_NO_PRIOR = 0x2
 
@@ -40,6 +44,7 @@ EXPORTS = (
     "glm_sync", "glm_selftest_wait_timeout", "glm_logpost_grad_noalloc",
     "glm_autotune_grouped", "glm_server_create", "glm_server_add_dataset", "glm_server_submit",
     "glm_server_poll", "glm_server_wait", "glm_server_stats", "glm_server_destroy",
+    "glm_server_remove_dataset",
     "glm_slice_create", "glm_slice_destroy", "glm_slice_eta", "glm_slice_coord_logpost",
     "glm_slice_run", "glm_slice_sync", "glm_ising_split", "glm_ising_merge", "glm_ising_sweeps",
     "glm_hess_create", "glm_hess_destroy", "glm_hess_eval", "glm_hess_sync",
@@ -72,14 +77,17 @@ class glm_server_desc_t(C.Structure):
 class glm_request_info_t(C.Structure):
     _fields_ = [("submit_ns", C.c_int64), ("start_ns", C.c_int64), ("done_ns", C.c_int64),
                 ("batch_k", C.c_int32), ("batch_requests", C.c_int32), ("k", C.c_int32),
-                ("status", C.c_int32)]
+                ("status", C.c_int32), ("path", C.c_int32), ("deferrals", C.c_int32)]
 
 
 class glm_server_stats_t(C.Structure):
     _fields_ = [("requests_done", C.c_int64), ("requests_failed", C.c_int64),
                 ("requests_waiting", C.c_int64), ("batches", C.c_int64),
                 ("vectors_done", C.c_int64), ("hbm_budget_bytes", C.c_int64),
-                ("hbm_in_flight_bytes", C.c_int64), ("max_concurrent_batches", C.c_int32),
+                ("hbm_in_flight_bytes", C.c_int64), ("hbm_resident_bytes", C.c_int64),
+                ("batches_tensor_cores", C.c_int64), ("deferrals", C.c_int64),
+                ("trimmed_batches", C.c_int64), ("refused_requests", C.c_int64),
+                ("max_concurrent_batches", C.c_int32),
                 ("last_cuda_error", C.c_int32), ("last_error_site", C.c_int32)]
 
 
@@ -129,6 +137,7 @@ def load(build_if_missing: bool = True):
             "glm_server_add_dataset": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32,
                                         C.c_int32, C.c_double, C.POINTER(C.c_int32)], st),
             "glm_server_submit": ([vp, C.c_int32, vp, C.c_int32, C.POINTER(C.c_uint64)], st),
+            "glm_server_remove_dataset": ([vp, C.c_int32], st),
             "glm_server_poll": ([vp, C.c_uint64, vp, vp, C.POINTER(glm_request_info_t)], st),
             "glm_server_wait": ([vp, C.c_uint64, vp, vp, C.POINTER(glm_request_info_t),
                                  C.c_int32], st),
@@ -292,6 +301,16 @@ def glm_server_add_dataset(s, X, x_scale, y, n_rows, p, ld, xtype=GLM_X_F32,
                                          int(ld), int(xtype), float(prior_sigma), C.byref(ds)),
            "glm_server_add_dataset")
     return ds.value
+
+
+def glm_server_remove_dataset(s, dataset_id) -> bool:
+    """Unregister a dataset; False (nothing changed) while requests for it
+    are still waiting or running."""
+    st = load().glm_server_remove_dataset(s, int(dataset_id))
+    if st == GLM_PENDING:
+        return False
+    _check(st, "glm_server_remove_dataset")
+    return True
 
 
 def glm_server_submit(s, dataset_id, beta_host, K) -> int:

@@ -462,12 +462,19 @@ glm_status_t glm_logpost_grad(glm_handle_t h, const void *X, const float *x_scal
         !aligned(f_out, 8) || !aligned(g_out, 4))
         return GLM_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    h->last_path = GLM_PATH_NONE;
     if (h->tc_enabled && K >= h->tc_min_k && h->d.xtype != GLM_X_F32) {
         st = launch_tc(h, X, x_scale, y, beta, K, f_out, g_out, s);
-        if (st != GLM_ERR_UNSUPPORTED)
+        if (st != GLM_ERR_UNSUPPORTED) {
+            if (st == GLM_OK)
+                h->last_path = GLM_PATH_TENSOR_CORES;
             return st;                  // else: the CUDA-core pass below
+        }
     }
-    return fused_eval(h, X, x_scale, y, beta, K, f_out, g_out, s);
+    st = fused_eval(h, X, x_scale, y, beta, K, f_out, g_out, s);
+    if (st == GLM_OK)
+        h->last_path = GLM_PATH_CUDA_CORES;
+    return st;
 }
 
 glm_status_t glm_logpost_grad_host(glm_handle_t h, const void *X, const float *x_scale,

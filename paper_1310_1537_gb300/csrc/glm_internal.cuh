@@ -131,6 +131,7 @@ struct glm_ctx {
     // tensor-core path
     int tc_enabled;
     int tc_min_k;
+    int last_path;              // glm_path_t of the last glm_logpost_grad launched
     alignas(64) unsigned char tc_map[128];   // CUtensorMap of the last X seen
     const void *tc_map_ptr;
     double *tc_part_f;          // per-CTA f partials

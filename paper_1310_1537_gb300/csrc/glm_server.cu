@@ -4,17 +4,34 @@
 // glm_server_submit and returned through glm_server_poll / glm_server_wait. A
 // scheduler thread forms batches: it takes the oldest waiting request, merges
 // later requests for the same dataset while the batch stays within
-// max_batch_k vectors, and launches the batch on a free stream slot as soon as
-// one is free and the batch's device buffers fit the HBM budget (admission by
-// free memory). Batches for different datasets run concurrently on different
-// streams; requests that arrive while others are on the GPU join the next
-// batch formed. Each slot copies its batch's coefficients in (pinned staging),
-// evaluates it with the dataset's handle for that slot, copies f and g out and
-// completes through a host callback that scatters results to the requests.
+// max_batch_k vectors, and launches the batch on a free stream slot once the
+// device memory account admits it. Batches for different datasets run
+// concurrently on different streams; requests that arrive while others are
+// on the GPU join the next batch formed. Each slot copies its batch's
+// coefficients in (pinned staging), evaluates it with the dataset's handle
+// for that slot, copies f and g out and completes through a host callback
+// that scatters results to the requests.
+//
+// Device memory account. One budget covers what the server stands for on the
+// device: every registered dataset (X, y, x_scale at their size, plus the
+// workspaces of its per-slot handles: "resident") and every running batch's
+// coefficient, f and g buffers ("in flight"). Batch buffers come from a
+// stream-ordered memory pool owned by the server (cudaMallocFromPoolAsync on
+// the slot's stream, freed on the same stream after the copies out), with
+// reuse across streams limited to frees that have completed, so the pool
+// never makes one slot's stream wait for another's. Admission: a dataset
+// that does not fit the budget is refused at registration; a request whose
+// batch could never fit is refused at submit; a batch that does not fit now
+// is trimmed to the requests that do, or deferred until a completion when
+// even the oldest request does not fit; a pool allocation the device cannot
+// serve defers the same way (or fails the request with GLM_ERR_OOM when
+// nothing is in flight that could give memory back).
+//
 // The evaluation of a vector does not depend on which other vectors share its
 // batch beyond the kernel path chosen for the batch size (CUDA cores below 16
-// vectors, tensor cores from 16), so a result alone and in a mix agree to the
-// evaluation tolerance.
+// vectors, tensor cores from 16 where the shape allows), so a result alone
+// and in a mix agree to the evaluation tolerance; each request reports the
+// path that served it.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -47,6 +64,9 @@ struct Dataset {
     int xtype;
     double sigma;
     std::vector<glm_handle_t> handles;      // one per slot
+    size_t footprint = 0;                   // bytes counted as resident
+    int outstanding = 0;                    // requests waiting or running
+    bool live = true;                       // false once removed
 };
 
 struct Request {
@@ -60,6 +80,9 @@ struct Request {
     int64_t done_ns = 0;
     int batch_k = 0;
     int batch_requests = 0;
+    int path = GLM_PATH_NONE;
+    int deferrals = 0;
+    bool deferred_now = false;              // counted in the current deferral
     int state = 0;                          // 0 waiting, 1 running, 2 done, 3 failed
     glm_status_t status = GLM_OK;
 };
@@ -80,8 +103,9 @@ struct Slot {
     std::vector<uint64_t> ids;
     int ds = -1;
     int K = 0;
-    size_t dev_off = 0;                     // arena offset of the batch buffers
-    size_t dev_bytes = 0;
+    void *dev = nullptr;                    // batch buffers from the pool
+    size_t dev_bytes = 0;                   // bytes counted as in flight
+    int path = GLM_PATH_NONE;
     glm_status_t launch_status = GLM_OK;
     int index = 0;                          // position in the slot pool
     struct glm_server *srv = nullptr;
@@ -97,19 +121,20 @@ struct glm_server {
     std::condition_variable done_cv;        // request completions
     std::vector<Dataset> datasets;
     std::map<uint64_t, Request> requests;
-    std::deque<uint64_t> waiting;
+    std::deque<uint64_t> waiting;           // request ids, ascending = arrival order
     std::vector<std::unique_ptr<Slot>> slots;
     uint64_t next_id = 1;
     bool stop = false;
     std::thread sched;
-    // device arena for batch buffers (first fit over a free list)
-    uint8_t *arena = nullptr;
-    size_t arena_bytes = 0;
-    std::vector<std::pair<size_t, size_t>> free_list;   // (offset, size)
+    cudaMemPool_t pool = nullptr;           // batch buffers
     std::vector<void *> retired;            // outgrown pinned staging buffers
-    size_t in_flight_bytes = 0;
+    // device memory account
+    size_t budget = 0;
+    size_t resident = 0;
+    size_t in_flight = 0;
     // statistics
     uint64_t n_done = 0, n_failed = 0, n_batches = 0, vectors_done = 0;
+    uint64_t n_batches_tc = 0, n_deferrals = 0, n_trimmed = 0, n_refused = 0;
     int max_concurrent = 0;
     int last_cuda_error = 0;                // cudaError_t of the last failed step
     int last_error_site = 0;                // glm_server_error_site_t of that step
@@ -117,46 +142,33 @@ struct glm_server {
 
 namespace {
 
-bool arena_alloc(glm_server *s, size_t bytes, size_t *off)
-{
-    bytes = (bytes + 255) / 256 * 256;
-    for (size_t i = 0; i < s->free_list.size(); ++i) {
-        if (s->free_list[i].second >= bytes) {
-            *off = s->free_list[i].first;
-            s->free_list[i].first += bytes;
-            s->free_list[i].second -= bytes;
-            if (s->free_list[i].second == 0)
-                s->free_list.erase(s->free_list.begin() + (long)i);
-            s->in_flight_bytes += bytes;
-            return true;
-        }
-    }
-    return false;
-}
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
-void arena_free(glm_server *s, size_t off, size_t bytes)
-{
-    bytes = (bytes + 255) / 256 * 256;
-    s->in_flight_bytes -= bytes;
-    s->free_list.push_back({off, bytes});
-    std::sort(s->free_list.begin(), s->free_list.end());
-    std::vector<std::pair<size_t, size_t>> merged;
-    for (auto &r : s->free_list) {
-        if (!merged.empty() && merged.back().first + merged.back().second == r.first)
-            merged.back().second += r.second;
-        else
-            merged.push_back(r);
-    }
-    s->free_list.swap(merged);
-}
-
+// Device bytes of a batch of K vectors of P coefficients: beta, f and g.
 size_t batch_bytes(int K, int p)
 {
-    return ((size_t)K * p * 4 + 255) / 256 * 256 + ((size_t)K * 8 + 255) / 256 * 256 +
-           ((size_t)K * p * 4 + 255) / 256 * 256;
+    return round256((size_t)K * p * 4) + round256((size_t)K * 8) + round256((size_t)K * p * 4);
 }
 
-// Host callback at the end of a batch: scatter results, free the slot.
+// What the budget leaves for batches (called with the lock held).
+size_t batch_room(const glm_server *s)
+{
+    const size_t used = s->resident + s->in_flight;
+    return used >= s->budget ? 0 : s->budget - used;
+}
+
+// Fail one waiting request (lock held); it is no longer in `waiting`.
+void fail_request(glm_server *s, Request &r, glm_status_t st)
+{
+    r.state = 3;
+    r.status = st;
+    r.done_ns = now_ns();
+    s->n_failed++;
+    s->datasets[(size_t)r.ds].outstanding--;
+}
+
+// Host callback at the end of a batch: scatter results, free the slot. The
+// batch buffers went back to the pool on the stream before this runs.
 void CUDART_CB batch_done(void *arg)
 {
     Slot *sl = static_cast<Slot *>(arg);
@@ -164,17 +176,21 @@ void CUDART_CB batch_done(void *arg)
     const int64_t t = now_ns();
     {
         std::lock_guard<std::mutex> lock(s->mu);
-        const int p = s->datasets[sl->ds].p;
+        Dataset &D = s->datasets[(size_t)sl->ds];
+        const int p = D.p;
         if (sl->launch_status == GLM_OK && (*sl->status_pin & glm::kDevTimeout)) {
             sl->launch_status = GLM_ERR_TIMEOUT;
             s->last_error_site = GLM_SERVER_SITE_DEVICE_WAIT;
         }
+        if (sl->launch_status == GLM_OK && sl->path == GLM_PATH_TENSOR_CORES)
+            s->n_batches_tc++;
         int k0 = 0;
         for (uint64_t id : sl->ids) {
             auto it = s->requests.find(id);
             if (it == s->requests.end())
                 continue;
             Request &r = it->second;
+            r.path = sl->launch_status == GLM_OK ? sl->path : GLM_PATH_NONE;
             if (sl->launch_status == GLM_OK) {
                 std::memcpy(r.f.data(), sl->b_f + k0, sizeof(double) * (size_t)r.K);
                 std::memcpy(r.g.data(), sl->b_g + (size_t)k0 * p, sizeof(float) * (size_t)r.K * p);
@@ -187,14 +203,35 @@ void CUDART_CB batch_done(void *arg)
                 s->n_failed++;
             }
             r.done_ns = t;
+            D.outstanding--;
             k0 += r.K;
         }
-        arena_free(s, sl->dev_off, sl->dev_bytes);
+        s->in_flight -= sl->dev_bytes;
+        sl->dev = nullptr;
+        sl->dev_bytes = 0;
         sl->busy = false;
         sl->ids.clear();
     }
     s->cv.notify_all();
     s->done_cv.notify_all();
+}
+
+// Put requests taken for a batch back into the queue in arrival order.
+void requeue_locked(glm_server *s, const std::vector<uint64_t> &ids)
+{
+    for (uint64_t id : ids)
+        s->waiting.push_back(id);
+    std::sort(s->waiting.begin(), s->waiting.end());
+}
+
+// Count one deferral episode for the request at the head of the queue.
+void note_deferral_locked(glm_server *s, Request &r)
+{
+    if (!r.deferred_now) {
+        r.deferred_now = true;
+        r.deferrals++;
+        s->n_deferrals++;
+    }
 }
 
 // Called with the lock held: form and launch batches while slots and memory allow.
@@ -211,75 +248,105 @@ void dispatch_locked(glm_server *s, std::unique_lock<std::mutex> &lock)
             }
         if (!sl)
             return;
-        // oldest waiting request decides the dataset; merge same-dataset requests
+        // the oldest waiting request decides the dataset
         const uint64_t first = s->waiting.front();
         Request &r0 = s->requests[first];
         const int ds = r0.ds;
-        const int p = s->datasets[ds].p;
+        const int p = s->datasets[(size_t)ds].p;
+        const size_t room = batch_room(s);
+        if (batch_bytes(r0.K, p) > room) {
+            if (s->in_flight == 0) {
+                // nothing running could give memory back: the budget shrank
+                // under it (datasets registered after it was queued)
+                s->waiting.pop_front();
+                s->n_refused++;
+                fail_request(s, r0, GLM_ERR_OOM);
+                s->done_cv.notify_all();
+                continue;
+            }
+            note_deferral_locked(s, r0);
+            return;                         // a completion wakes the scheduler
+        }
+        // merge later same-dataset requests that keep the batch within
+        // max_batch_k vectors and within the room the budget leaves
         std::vector<uint64_t> ids;
         int K = 0;
+        bool trimmed = false;
         for (auto it = s->waiting.begin(); it != s->waiting.end();) {
             Request &r = s->requests[*it];
             if (r.ds == ds && K + r.K <= s->d.max_batch_k) {
-                ids.push_back(*it);
-                K += r.K;
-                it = s->waiting.erase(it);
-            } else {
-                ++it;
+                if (batch_bytes(K + r.K, p) <= room) {
+                    ids.push_back(*it);
+                    K += r.K;
+                    it = s->waiting.erase(it);
+                    continue;
+                }
+                trimmed = true;
             }
+            ++it;
         }
         const size_t bytes = batch_bytes(K, p);
-        size_t off = 0;
-        if (!arena_alloc(s, bytes, &off)) {
-            // not enough free device memory right now: put the batch back in
-            // arrival order and wait for a completion
-            for (auto it = ids.rbegin(); it != ids.rend(); ++it)
-                s->waiting.push_front(*it);
-            std::sort(s->waiting.begin(), s->waiting.end());
-            return;
-        }
+        s->in_flight += bytes;              // reserved before the lock is dropped
         sl->busy = true;
         sl->ids = ids;
         sl->ds = ds;
         sl->K = K;
-        sl->dev_off = off;
+        sl->dev = nullptr;
         sl->dev_bytes = bytes;
+        sl->path = GLM_PATH_NONE;
         sl->launch_status = GLM_OK;
         sl->b_beta = sl->beta_pin;
         sl->b_f = sl->f_pin;
         sl->b_g = sl->g_pin;
-        int busy_now = 0;
-        for (auto &u : s->slots)
-            busy_now += u->busy ? 1 : 0;
-        s->max_concurrent = std::max(s->max_concurrent, busy_now);
-        s->n_batches++;
-        const int64_t t = now_ns();
         int k0 = 0;
         for (uint64_t id : ids) {
             Request &r = s->requests[id];
-            r.state = 1;
-            r.start_ns = t;
-            r.batch_k = K;
-            r.batch_requests = (int)ids.size();
             std::memcpy(sl->b_beta + (size_t)k0 * p, r.beta.data(), sizeof(float) * (size_t)r.K * p);
             k0 += r.K;
         }
         // copy what the launch needs: add_dataset may grow the vector meanwhile
-        const Dataset &D = s->datasets[ds];
+        const Dataset &D = s->datasets[(size_t)ds];
         glm_handle_t h = D.handles[(size_t)sl->index];
         const void *X = D.X;
         const float *x_scale = D.x_scale;
         const uint8_t *y = D.y;
-        uint8_t *base = s->arena + off;
-        float *dbeta = reinterpret_cast<float *>(base);
-        double *df = reinterpret_cast<double *>(base + ((size_t)K * p * 4 + 255) / 256 * 256);
-        float *dg = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(df) +
-                                              ((size_t)K * 8 + 255) / 256 * 256);
-        // launch without the lock: the callback takes it
+        // allocate and launch without the lock: the callback takes it
         lock.unlock();
+        void *dev = nullptr;
+        cudaError_t ce = cudaMallocFromPoolAsync(&dev, bytes, s->pool, sl->stream);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            lock.lock();
+            s->in_flight -= bytes;
+            sl->busy = false;
+            sl->ids.clear();
+            requeue_locked(s, ids);
+            Request &h0 = s->requests[s->waiting.front()];
+            if (s->in_flight == 0) {
+                // the device cannot give even this with nothing else running
+                for (uint64_t id : ids) {
+                    auto w = std::find(s->waiting.begin(), s->waiting.end(), id);
+                    if (w != s->waiting.end())
+                        s->waiting.erase(w);
+                    s->n_refused++;
+                    fail_request(s, s->requests[id], GLM_ERR_OOM);
+                }
+                s->last_cuda_error = (int)ce;
+                s->last_error_site = GLM_SERVER_SITE_COPY_IN;
+                s->done_cv.notify_all();
+                continue;
+            }
+            note_deferral_locked(s, h0);
+            return;
+        }
+        sl->dev = dev;
+        uint8_t *base = static_cast<uint8_t *>(dev);
+        float *dbeta = reinterpret_cast<float *>(base);
+        double *df = reinterpret_cast<double *>(base + round256((size_t)K * p * 4));
+        float *dg = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(df) +
+                                              round256((size_t)K * 8));
         glm_status_t st = GLM_OK;
         int site = 0;
-        cudaError_t ce = cudaSuccess;
         *sl->status_pin = 0;
         if ((ce = cudaMemcpyAsync(dbeta, sl->b_beta, sizeof(float) * (size_t)K * p,
                                   cudaMemcpyHostToDevice, sl->stream)) != cudaSuccess) {
@@ -292,6 +359,8 @@ void dispatch_locked(glm_server *s, std::unique_lock<std::mutex> &lock)
             if (st != GLM_OK) {
                 site = GLM_SERVER_SITE_EVALUATE;
                 ce = cudaGetLastError();
+            } else {
+                sl->path = h->last_path;    // this slot's handle: only this thread uses it
             }
         }
         if (st == GLM_OK &&
@@ -305,11 +374,31 @@ void dispatch_locked(glm_server *s, std::unique_lock<std::mutex> &lock)
             st = GLM_ERR_CUDA;
             site = GLM_SERVER_SITE_COPY_OUT;
         }
+        // back to the pool once the stream has passed the copies
+        if (cudaFreeAsync(dev, sl->stream) != cudaSuccess)
+            cudaGetLastError();
         sl->launch_status = st;
-        if (st != GLM_OK) {
+        {
             std::lock_guard<std::mutex> g(s->mu);
-            s->last_cuda_error = (int)ce;
-            s->last_error_site = site;
+            if (st != GLM_OK) {
+                s->last_cuda_error = (int)ce;
+                s->last_error_site = site;
+            }
+            int busy_now = 0;
+            for (auto &u : s->slots)
+                busy_now += u->busy ? 1 : 0;
+            s->max_concurrent = std::max(s->max_concurrent, busy_now);
+            s->n_batches++;
+            s->n_trimmed += trimmed ? 1 : 0;
+            const int64_t t = now_ns();
+            for (uint64_t id : ids) {
+                Request &r = s->requests[id];
+                r.state = 1;
+                r.start_ns = t;
+                r.batch_k = K;
+                r.batch_requests = (int)ids.size();
+                r.deferred_now = false;
+            }
         }
         if ((ce = cudaLaunchHostFunc(sl->stream, batch_done, sl)) != cudaSuccess) {
             cudaGetLastError();
@@ -395,24 +484,42 @@ glm_status_t glm_server_create(const glm_server_desc_t *desc, glm_server_t *out)
     }
     if (desc->device >= ndev || cudaSetDevice(desc->device) != cudaSuccess)
         return GLM_ERR_INVALID_ARG;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return GLM_ERR_CUDA;
+    }
+    const size_t budget = desc->hbm_budget_bytes > 0 ? (size_t)desc->hbm_budget_bytes
+                                                     : free_b - free_b / 16;
+    if (budget < 65536)
+        return GLM_ERR_OOM;
     glm_server *s = new (std::nothrow) glm_server;
     if (!s)
         return GLM_ERR_OOM;
     s->d = *desc;
     s->device = desc->device;
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    size_t budget = desc->hbm_budget_bytes > 0 ? (size_t)desc->hbm_budget_bytes : free_b / 8;
-    if (budget > free_b / 2)
-        budget = free_b / 2;
-    budget = budget / 256 * 256;
-    if (budget < 4096 || cudaMalloc((void **)&s->arena, budget) != cudaSuccess) {
+    s->budget = budget;
+    // batch buffers: a pool that keeps what it got from the device (no
+    // release threshold) and reuses a block across streams only once its free
+    // has completed, never by making one stream wait for another
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = desc->device;
+    uint64_t keep = ~0ull;
+    int no = 0;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no) !=
+            cudaSuccess) {
         cudaGetLastError();
+        if (s->pool)
+            cudaMemPoolDestroy(s->pool);
         delete s;
         return GLM_ERR_OOM;
     }
-    s->arena_bytes = budget;
-    s->free_list.push_back({0, budget});
     for (int i = 0; i < desc->streams; ++i) {
         auto sl = std::make_unique<Slot>();
         sl->srv = s;
@@ -421,7 +528,7 @@ glm_status_t glm_server_create(const glm_server_desc_t *desc, glm_server_t *out)
             cudaGetLastError();
             for (auto &u : s->slots)
                 cudaStreamDestroy(u->stream);
-            cudaFree(s->arena);
+            cudaMemPoolDestroy(s->pool);
             delete s;
             return GLM_ERR_CUDA;
         }
@@ -456,30 +563,84 @@ glm_status_t glm_server_add_dataset(glm_server_t s, const void *X, const float *
     hd.xtype = xtype;
     hd.prior_sigma = prior_sigma;
     hd.device = s->device;
-    for (size_t i = 0; i < s->slots.size(); ++i) {
-        glm_handle_t h = nullptr;
-        glm_status_t st = glm_create(&hd, &h);
-        if (st != GLM_OK) {
-            for (auto hh : D.handles)
-                glm_destroy(hh);
-            return st;
+    // the first handle validates the shape and gives the workspace size
+    glm_handle_t h0 = nullptr;
+    glm_status_t st = glm_create(&hd, &h0);
+    if (st != GLM_OK)
+        return st;
+    glm_info_t info;
+    glm_get_info(h0, &info);
+    const size_t nslots = s->slots.size();
+    const size_t es = xtype == GLM_X_F32 ? 4 : xtype == GLM_X_BF16 ? 2 : 1;
+    const size_t data = round256((size_t)n_rows * (size_t)ld * es) + round256((size_t)n_rows) +
+                        (x_scale ? round256((size_t)p * 4) : 0);
+    D.footprint = data + (size_t)info.workspace_bytes * nslots;
+    {
+        // reserve the footprint before the other handles allocate
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->resident + s->in_flight + D.footprint + batch_bytes(1, p) > s->budget) {
+            glm_destroy(h0);
+            return GLM_ERR_OOM;
         }
+        s->resident += D.footprint;
+    }
+    auto undo = [&](glm_status_t e) {
+        for (auto hh : D.handles)
+            glm_destroy(hh);
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->resident -= D.footprint;
+        return e;
+    };
+    D.handles.push_back(h0);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return undo(GLM_ERR_CUDA);
+    }
+    if ((size_t)info.workspace_bytes * (nslots - 1) + ((size_t)16 << 20) > free_b)
+        return undo(GLM_ERR_OOM);           // the device has not got the workspaces
+    for (size_t i = 1; i < nslots; ++i) {
+        glm_handle_t h = nullptr;
+        st = glm_create(&hd, &h);
+        if (st != GLM_OK)
+            return undo(st);
         D.handles.push_back(h);
     }
-    std::lock_guard<std::mutex> lock(s->mu);
-    glm_status_t st = ensure_slot_capacity(s, p);
-    if (st != GLM_OK) {
-        for (auto hh : D.handles)
-            glm_destroy(hh);
-        return st;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        st = ensure_slot_capacity(s, p);
+        if (st == GLM_OK) {
+            *dataset_id = (int32_t)s->datasets.size();
+            s->datasets.push_back(std::move(D));
+            return GLM_OK;
+        }
     }
-    if (batch_bytes(s->d.max_batch_k, p) > s->arena_bytes) {
-        for (auto hh : D.handles)
-            glm_destroy(hh);
-        return GLM_ERR_OOM;
+    // glm_destroy synchronises the device, which waits for completion
+    // callbacks that take the lock: never destroy with the lock held
+    return undo(st);
+}
+
+glm_status_t glm_server_remove_dataset(glm_server_t s, int32_t dataset_id)
+{
+    if (!s)
+        return GLM_ERR_INVALID_ARG;
+    std::vector<glm_handle_t> handles;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (dataset_id < 0 || dataset_id >= (int32_t)s->datasets.size() ||
+            !s->datasets[(size_t)dataset_id].live)
+            return GLM_ERR_INVALID_ARG;
+        Dataset &D = s->datasets[(size_t)dataset_id];
+        if (D.outstanding > 0)
+            return GLM_PENDING;
+        D.live = false;
+        handles.swap(D.handles);
+        s->resident -= D.footprint;
+        D.footprint = 0;
     }
-    *dataset_id = (int32_t)s->datasets.size();
-    s->datasets.push_back(std::move(D));
+    for (auto h : handles)
+        glm_destroy(h);
+    s->cv.notify_all();                     // memory came back: deferred work may fit
     return GLM_OK;
 }
 
@@ -492,12 +653,17 @@ glm_status_t glm_server_submit(glm_server_t s, int32_t dataset_id, const float *
     uint64_t id;
     {
         std::lock_guard<std::mutex> lock(s->mu);
-        if (dataset_id < 0 || dataset_id >= (int32_t)s->datasets.size() || K < 1 ||
-            K > s->d.max_batch_k)
+        if (dataset_id < 0 || dataset_id >= (int32_t)s->datasets.size() ||
+            !s->datasets[(size_t)dataset_id].live || K < 1 || K > s->d.max_batch_k)
             return GLM_ERR_INVALID_ARG;
         if ((int)s->waiting.size() >= s->d.max_pending)
             return GLM_ERR_OOM;   // queue full: refuse rather than grow without bound
-        const int p = s->datasets[dataset_id].p;
+        Dataset &D = s->datasets[(size_t)dataset_id];
+        const int p = D.p;
+        if (s->resident >= s->budget || batch_bytes(K, p) > s->budget - s->resident) {
+            s->n_refused++;
+            return GLM_ERR_OOM;   // could not fit even with nothing in flight
+        }
         id = s->next_id++;
         Request &r = s->requests[id];
         r.ds = dataset_id;
@@ -506,6 +672,7 @@ glm_status_t glm_server_submit(glm_server_t s, int32_t dataset_id, const float *
         r.f.assign((size_t)K, 0.0);
         r.g.assign((size_t)K * p, 0.0f);
         r.submit_ns = t;
+        D.outstanding++;
         s->waiting.push_back(id);
     }
     s->cv.notify_all();
@@ -525,6 +692,8 @@ static glm_status_t take_result(glm_server_t s, Request &r, double *f_host, floa
         info->batch_requests = r.batch_requests;
         info->k = r.K;
         info->status = r.state == 2 ? GLM_OK : r.status;
+        info->path = r.path;
+        info->deferrals = r.deferrals;
     }
     if (r.state == 2) {
         if (f_host)
@@ -587,11 +756,16 @@ glm_status_t glm_server_stats(glm_server_t s, glm_server_stats_t *st)
     st->requests_waiting = (int64_t)s->waiting.size();
     st->batches = (int64_t)s->n_batches;
     st->vectors_done = (int64_t)s->vectors_done;
+    st->hbm_budget_bytes = (int64_t)s->budget;
+    st->hbm_in_flight_bytes = (int64_t)s->in_flight;
+    st->hbm_resident_bytes = (int64_t)s->resident;
+    st->batches_tensor_cores = (int64_t)s->n_batches_tc;
+    st->deferrals = (int64_t)s->n_deferrals;
+    st->trimmed_batches = (int64_t)s->n_trimmed;
+    st->refused_requests = (int64_t)s->n_refused;
     st->max_concurrent_batches = s->max_concurrent;
     st->last_cuda_error = s->last_cuda_error;
     st->last_error_site = s->last_error_site;
-    st->hbm_budget_bytes = (int64_t)s->arena_bytes;
-    st->hbm_in_flight_bytes = (int64_t)s->in_flight_bytes;
     return GLM_OK;
 }
 
@@ -622,7 +796,7 @@ glm_status_t glm_server_destroy(glm_server_t s)
     }
     for (void *p : s->retired)
         cudaFreeHost(p);
-    cudaFree(s->arena);
+    cudaMemPoolDestroy(s->pool);
     delete s;
     return GLM_OK;
 }

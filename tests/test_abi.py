@@ -100,6 +100,7 @@ def test_server_rejects_bad_descriptors_and_null_arguments():
                                       C.byref(ds)) == pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_server_poll(None, 1, None, None, None) == pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_server_stats(None, None) == pkg.GLM_ERR_INVALID_ARG
+    assert lib.glm_server_remove_dataset(None, 0) == pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_server_destroy(None) == pkg.GLM_OK
     assert pkg.glm_status_str(pkg.GLM_PENDING) == "pending"
 
@@ -160,3 +161,40 @@ def test_hessian_evaluator_rejects_bad_shapes_without_a_device():
     assert lib.glm_hess_create(10, 8, 8, 1.0, 0, None) == pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_hess_eval(None, None, None, None, None, None, None, None) == pkg.GLM_ERR_INVALID_ARG
     assert lib.glm_hess_destroy(None) == pkg.GLM_OK
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every structure the binding mirrors has the header's size and field
+    offsets, as a C compiler lays them out."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [pkg.glm_desc_t, pkg.glm_info_t, pkg.glm_server_desc_t, pkg.glm_request_info_t,
+               pkg.glm_server_stats_t, pkg.glm_slice_desc_t]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "glm.h"', 'int main(void) {']
+    for st in structs:
+        t = st.__name__
+        lines.append(f'printf("{t} size %zu\\n", sizeof({t}));')
+        for name, _ in st._fields_:
+            lines.append(f'printf("{t} {name} %zu\\n", offsetof({t}, {name}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for st in structs:
+        t = st.__name__
+        assert int(got[f"{t} size"]) == C_sizeof(st), t
+        for name, _ in st._fields_:
+            assert int(got[f"{t} {name}"]) == getattr(st, name).offset, (t, name)
+
+
+def C_sizeof(st):
+    import ctypes
+    return ctypes.sizeof(st)
