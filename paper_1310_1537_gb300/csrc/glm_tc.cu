@@ -41,7 +41,6 @@ constexpr int kTcRows = 128;
 constexpr int kTcEpiWarps = 16;
 constexpr int kTcEpiGroups = kTcEpiWarps / 4;       // warps per tensor-memory lane quarter
 constexpr int kTcEpiCols = 128 / kTcEpiGroups;      // D1 columns (tile rows) per warp
-constexpr int kTcEpiRows = kTcEpiCols / 2;          // rows per thread
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTcMaxStages = 4;
 constexpr int kTcMaxP = 256;
@@ -81,19 +80,28 @@ __host__ __device__ constexpr uint32_t idesc_f16kind(int n, int a_mn, int b_mn, 
 }
 
 // TR map on the hardware base-2 exponential and logarithm, overflow-free:
-// with e = exp(-|eta|) and L = log2(1 + e),
-//   ell = y eta - max(eta, 0) - L ln 2,
-//   sigma(eta) = exp(min(eta, 0)) / (1 + e) = 2^(min(eta, 0) log2(e) - L),
+// with e = exp(-|z|) and L = log2(1 + e),
+//   softplus(z) = max(z, 0) + L ln 2,
+//   sigma(z) = exp(min(z, 0)) / (1 + e) = 2^(min(z, 0) log2(e) - L),
 // so the logistic needs one more exponential and no reciprocal or select.
-__device__ __forceinline__ void tr_fast(float eta, float yv, float &ell, float &r)
+// TR map with the label folded into a sign: z = (1 - 2y) eta, so that
+// ell = -softplus(z) and r = y - sigma(eta) = (2y - 1) sigma(z); ysh holds the
+// label in its sign bit. Adds ell to facc and returns r split into BF16 terms
+// hi = round(r), lo = round(r - hi), packed hi in the low half.
+__device__ __forceinline__ uint32_t tr_pack(float eta, uint32_t ysh, float &facc)
 {
     constexpr float kLog2e = 1.4426950408889634f;
     constexpr float kLn2 = 0.69314718055994531f;
-    const float e = ex2_approx(-fabsf(eta) * kLog2e);     // exp(-|eta|) in (0, 1]
+    const float z = __uint_as_float(__float_as_uint(eta) ^ (ysh & 0x80000000u));
+    const float e = ex2_approx(-fabsf(z) * kLog2e);       // exp(-|z|) in (0, 1]
     const float L = lg2_approx(1.0f + e);
-    ell = fmaf(yv, eta, -fmaxf(eta, 0.0f));
-    ell = fmaf(-kLn2, L, ell);
-    r = yv - ex2_approx(fmaf(fminf(eta, 0.0f), kLog2e, -L));
+    facc -= fmaxf(z, 0.0f);
+    facc = fmaf(-kLn2, L, facc);
+    const float sg = ex2_approx(fmaf(fminf(z, 0.0f), kLog2e, -L));   // sigma(z)
+    const float r = __uint_as_float(__float_as_uint(sg) ^ (~ysh & 0x80000000u));
+    const float hi = __bfloat162float(__float2bfloat16_rn(r));
+    __nv_bfloat162 v = __floats2bfloat162_rn(hi, r - hi);
+    return *reinterpret_cast<uint32_t *>(&v);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -223,16 +231,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // beta into tensor memory: lane n = 2k + part holds the hi (part 0) or lo
-    // (part 1) term of beta_k, two columns of beta per 32-bit cell. FP8
-    // storage: the coefficients are s_j beta_kj times 2^e_k, with e_k the
-    // power of two that brings max_j |s_j beta_kj| just under 2^14.
+    // beta into tensor memory, two columns of beta per 32-bit cell. Lanes go
+    // in groups of 16: in lane quarter q, group g holds vectors
+    // k = 16q + 8g + v (v = 0..7), the hi term of beta_k in lane 16g + v and
+    // the lo term eight lanes further. A 16x256b tensor-memory load then gives
+    // each epilogue thread both partial sums of one (row, vector) pair, so
+    // they add in registers with no exchange between lanes.
     constexpr int EPI0 = 2;                         // first epilogue warp
     if (warp >= EPI0 && warp < EPI0 + 4) {
         const int q = warp & 3;
-        const int n = q * 32 + lane;
-        const int k = n >> 1;
-        const int part = n & 1;
+        const int k = 16 * q + 8 * (lane >> 4) + (lane & 7);
+        const int part = (lane >> 3) & 1;
         for (int cb = 0; cb < PA * 32; cb += 32) {
             uint32_t r[32];
 #pragma unroll
@@ -339,51 +348,57 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     } else {
         // ---- epilogue ---------------------------------------------------------------------
+        // Warp (q, hh): lane quarter q (vectors 16q .. 16q + 15) and tile rows
+        // CW hh .. CW hh + 31. Thread (tq, tr) = (lane / 4, lane % 4) takes the
+        // vectors k = 16q + tq and k + 8 on the rows CW hh + 8m + 2tr + j
+        // (m = 0..3, j = 0, 1): 16 (row, vector) pairs per tile, each read as
+        // its hi and lo partial sums by two 16x256b loads.
         constexpr int CW = kTcEpiCols;
-        constexpr int RT = kTcEpiRows;
-        const int q = warp & 3;                 // tensor-memory lane quarter
-        const int hh = (warp - EPI0) >> 2;      // tile rows CW*hh .. CW*hh + CW - 1
-        const int n = q * 32 + lane;            // D1 lane
-        const int k = n >> 1;                   // vector
-        const int part = n & 1;                 // 0: beta_hi lane, 1: beta_lo lane
-        const bool active = k < p.kk;
-        const int tb = CW * hh + RT * part;     // this thread's RT rows
-        // the lo lane walks its rows rotated by 4 (row (j + 4) mod 16 at step
-        // j): its R-tile stores then fall in other 16-byte chunks of the
-        // swizzle than the hi lane's, and the two halves do not conflict
-        const int rot = part ? 4 : 0;
-        float facc = 0.0f;
-        uint32_t yw[RT / 4], yn[RT / 4];
+        const int q = warp & 3;
+        const int hh = (warp - EPI0) >> 2;
+        const int tq = lane >> 2;
+        const int tr = lane & 3;
+        const int kq = 16 * q + tq;
+        const int row_t = CW * hh + 2 * tr;     // this thread's first row in the tile
+        // the label of row row_t + 8m + j is byte 2(tr & 1) + j of word m below;
+        // shifted so that its low bit is the sign bit
+        const uint32_t sh0 = 31u - 16u * (uint32_t)(tr & 1);
+        const uint32_t sh1 = sh0 - 8u;
+        // R tile stores: row row_t + 8m + j, columns 2k (hi) and 2k + 1 (lo) of
+        // 64-column region k / 32, with the 128B swizzle of 16-byte chunks by
+        // row & 7 = 2tr + j; conflict-free across the warp
+        uint32_t roff[2][2];
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const uint32_t chunk = (uint32_t)(4 * (q & 1) + 2 * g + (tq >> 2));
+                roff[g][j] = (uint32_t)((q >> 1) * 16384 + (row_t + j) * 128 + (tq & 3) * 4) +
+                             ((chunk ^ (uint32_t)(2 * tr + j)) << 4);
+            }
+        float facc0 = 0.0f, facc1 = 0.0f;
+        uint32_t yw[4], yn[4];
         auto load_y = [&](int i, uint32_t *dst) {
 #pragma unroll
-            for (int w = 0; w < RT / 4; ++w)
-                dst[w] = 0u;
+            for (int m = 0; m < 4; ++m)
+                dst[m] = 0u;
             if (i >= nt)
                 return;
-            const int64_t r0 = (int64_t)(b + (int64_t)i * grid) * kTcRows + tb;
-            if (p.y_al4 && r0 + RT <= p.N) {
+            const int64_t t0 = (int64_t)(b + (int64_t)i * grid) * kTcRows;
+            const int64_t r0 = t0 + CW * hh + 4 * (tr >> 1);     // word m: rows r0 + 8m ..
+            if (p.y_al4 && t0 + kTcRows <= p.N) {
                 const uint32_t *yp = reinterpret_cast<const uint32_t *>(p.y + r0);
 #pragma unroll
-                for (int w = 0; w < RT / 4; ++w)
-                    dst[w] = __ldg(yp + w);
+                for (int m = 0; m < 4; ++m)
+                    dst[m] = __ldg(yp + 2 * m);
             } else {
-                for (int j = 0; j < RT; ++j)
-                    if (r0 + j < p.N)
-                        dst[j >> 2] |= (uint32_t)__ldg(p.y + r0 + j) << (8 * (j & 3));
-            }
-        };
-        // labels in the lo lane's row order: words rotated by one
-        auto rotate_y = [&](uint32_t *y4) {
-            if (part) {
-                const uint32_t t0 = y4[0];
-#pragma unroll
-                for (int w = 0; w < RT / 4 - 1; ++w)
-                    y4[w] = y4[w + 1];
-                y4[RT / 4 - 1] = t0;
+                for (int m = 0; m < 4; ++m)
+                    for (int c = 0; c < 4; ++c)
+                        if (r0 + 8 * m + c < p.N)
+                            dst[m] |= (uint32_t)__ldg(p.y + r0 + 8 * m + c) << (8 * c);
             }
         };
         load_y(0, yw);
-        rotate_y(yw);
         bool ok = true;
         for (int i = 0; i < nt; ++i) {
             load_y(i + 1, yn);
@@ -392,78 +407,60 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc::fence_after();
-            float v[CW];
-            tc::tmem_ld<CW>(tmem + ((uint32_t)(q * 32) << 16) + kTcD1Col + CW * hh, v);
+            float v0[16], v1[16];
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + kTcD1Col + CW * hh;
+            tc::tmem_ld16x256_x4(ta, v0);
+            tc::tmem_ld16x256_x4(ta + (16u << 16), v1);
             tc::tmem_wait_ld();
             tc::fence_before();
             __syncwarp();
             if (lane == 0)
                 ptx::mbar_arrive(d1_empty);
-            const int64_t rbase = (int64_t)(b + (int64_t)i * grid) * kTcRows + tb;
-            const int64_t left = p.N - rbase;
-            const int nvalid = !active ? 0 : (left >= RT ? RT : (left > 0 ? (int)left : 0));
-            uint32_t w[RT];
-            // hi/lo lanes of a vector each keep their own RT rows: swap the
-            // other half with the partner lane and add
-            float mine[RT];
+            const int64_t left = p.N - (int64_t)(b + (int64_t)i * grid) * kTcRows;
+            uint32_t w0[8], w1[8];              // packed (hi, lo) residuals, index 2m + j
+            if (left >= kTcRows) {
 #pragma unroll
-            for (int j = 0; j < RT; ++j) {
-                const int pj = (j + 4) & (RT - 1);
-                const float send = part ? v[j] : v[RT + pj];
-                mine[j] = (part ? v[RT + pj] : v[j]) + __shfl_xor_sync(0xFFFFFFFFu, send, 1);
-            }
-            if (nvalid == RT) {
+                for (int m = 0; m < 4; ++m)
 #pragma unroll
-                for (int j = 0; j < RT; ++j) {
-                    const float yv = (float)((yw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
-                    float ell, r;
-                    tc::tr_fast(mine[j], yv, ell, r);
-                    facc += ell;
-                    float rh, rl;
-                    tc::split2<FP8>(r, rh, rl);
-                    w[j] = tc::pack2<FP8>(rh, rl);
-                }
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t ysh = yw[m] << (j ? sh1 : sh0);
+                        w0[2 * m + j] = tc::tr_pack(v0[4 * m + j] + v0[4 * m + 2 + j], ysh, facc0);
+                        w1[2 * m + j] = tc::tr_pack(v1[4 * m + j] + v1[4 * m + 2 + j], ysh, facc1);
+                    }
             } else {
 #pragma unroll
-                for (int j = 0; j < RT; ++j) {
-                    const float yv = (float)((yw[j >> 2] >> (8 * (j & 3))) & 0xFFu);
-                    float ell, r;
-                    tc::tr_fast(mine[j], yv, ell, r);
-                    const bool in = ((j + rot) & (RT - 1)) < nvalid;
-                    facc += in ? ell : 0.0f;
-                    r = in ? r : 0.0f;
-                    float rh, rl;
-                    tc::split2<FP8>(r, rh, rl);
-                    w[j] = tc::pack2<FP8>(rh, rl);
-                }
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t ysh = yw[m] << (j ? sh1 : sh0);
+                        const bool in = row_t + 8 * m + j < left;
+                        float f0 = 0.0f, f1 = 0.0f;
+                        const uint32_t a0 = tc::tr_pack(v0[4 * m + j] + v0[4 * m + 2 + j], ysh, f0);
+                        const uint32_t a1 = tc::tr_pack(v1[4 * m + j] + v1[4 * m + 2 + j], ysh, f1);
+                        w0[2 * m + j] = in ? a0 : 0u;
+                        w1[2 * m + j] = in ? a1 : 0u;
+                        facc0 += in ? f0 : 0.0f;
+                        facc1 += in ? f1 : 0.0f;
+                    }
             }
             if (i >= 1 && !ptx::mbar_wait_bounded(r_empty, (unsigned)(i - 1) & 1u, kSpinLimit)) {
                 ok = false;
                 break;
             }
-            // R tile rows tb..tb+RT-1 (tb is a multiple of 8), columns 2k (hi)
-            // and 2k+1 (lo): the 128B swizzle permutes 16-byte chunks by row & 7
-            const uint32_t rrow = (uint32_t)((k >> 5) * 16384 + tb * 128 + (((2 * k) & 7) << 1));
-            const uint32_t chunk = (uint32_t)((2 * k) & 63) >> 3;
-            // row (j + rot) mod 16: (j + 4) & 7 = (j & 7) ^ 4, so the lo lane
-            // uses the hi lane's addressing with its chunk flipped by 4 and
-            // its base moved by 4 rows (back 12 rows from step 12 on)
-            const uint32_t chk = chunk ^ (uint32_t)rot;
-            const uint32_t base_a = rrow + (uint32_t)(rot * 128);
-            const uint32_t base_b = base_a - (uint32_t)(rot * 512);
 #pragma unroll
-            for (int j = 0; j < RT; ++j) {
-                const uint32_t bj = (j < RT - 4) ? base_a : base_b;
-                *reinterpret_cast<uint32_t *>(rb + (bj + j * 128 + ((chk ^ (uint32_t)(j & 7)) << 4))) = w[j];
-            }
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    *reinterpret_cast<uint32_t *>(rb + roff[0][j] + m * 1024) = w0[2 * m + j];
+                    *reinterpret_cast<uint32_t *>(rb + roff[1][j] + m * 1024) = w1[2 * m + j];
+                }
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0)
                 ptx::mbar_arrive(r_full);
 #pragma unroll
-            for (int t = 0; t < RT / 4; ++t)
-                yw[t] = yn[t];
-            rotate_y(yw);
+            for (int m = 0; m < 4; ++m)
+                yw[m] = yn[m];
         }
         if (!ok) {
             atomicOr(p.status, kDevTimeout);
@@ -492,11 +489,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         have ? gv[2 * kk2] + gv[2 * kk2 + 1] : 0.0f;
             }
         }
-        // f partial: the two lanes of a vector, then the row groups in order
+        // f partial: the four lanes of a vector, then the row groups in order
+        double f0 = (double)facc0, f1 = (double)facc1;
+        f0 += __shfl_xor_sync(0xFFFFFFFFu, f0, 1);
+        f1 += __shfl_xor_sync(0xFFFFFFFFu, f1, 1);
+        f0 += __shfl_xor_sync(0xFFFFFFFFu, f0, 2);
+        f1 += __shfl_xor_sync(0xFFFFFFFFu, f1, 2);
         asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
-        const double fv = (double)facc + __shfl_xor_sync(0xFFFFFFFFu, (double)facc, 1);
-        if (part == 0)
-            sf[hh * 64 + k] = fv;
+        if (tr == 0) {
+            sf[hh * 64 + kq] = f0;
+            sf[hh * 64 + kq + 8] = f1;
+        }
         asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32) : "memory");
         const int et = tid - 32 * EPI0;
         if (et < p.kk) {

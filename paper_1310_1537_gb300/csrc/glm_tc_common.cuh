@@ -118,6 +118,24 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float *v)
         v[i] = __uint_as_float(r[i]);
 }
 
+// 16 lanes x 256 bits, four repetitions along the columns (16 registers):
+// thread t reads lanes base + t/4 and base + t/4 + 8; in repetition i,
+// v[4i], v[4i+1] are columns 8i + 2(t%4) and 8i + 2(t%4) + 1 of the first
+// lane and v[4i+2], v[4i+3] the same columns of the second.
+__device__ __forceinline__ void tmem_ld16x256_x4(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r)
