@@ -392,8 +392,14 @@ __global__ void __launch_bounds__(kHThreads, 1)
 // each add a contiguous range of CTAs with all loads of a range in flight,
 // then warp 0 adds the 8 range sums in order. H_ij is written to both
 // triangles (exactly symmetric).
-constexpr int kHessRedWarps = 8;
+constexpr int kHessRedWarps = 16;
 
+// Fixed-order combine of the per-CTA partials: a block takes 32 outputs (f,
+// an entry of g, or an upper-triangle entry of H), each of its warps adds a
+// contiguous range of CTAs (all loads of a range in flight) and warp 0 adds
+// the warps' sums in order. g and H are summed in FP32 (152 partials: a
+// relative rounding error of order 1e-6; this part's FP64 pipe made the FP64
+// version 4x slower), f in FP64.
 __global__ void __launch_bounds__(32 * kHessRedWarps)
     hess_combine_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g,
                         const float *__restrict__ part_h, int parts, int P,
@@ -402,7 +408,8 @@ __global__ void __launch_bounds__(32 * kHessRedWarps)
                         float *__restrict__ H_out)
 {
     ptx::grid_dep_wait();
-    __shared__ double sum[kHessRedWarps][32];
+    __shared__ float sum[kHessRedWarps][32];
+    __shared__ double fsum[kHessRedWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nel = 1 + kHMaxP + kHMaxP * kHMaxP;
     const int e = blockIdx.x * 32 + lane;
@@ -418,46 +425,55 @@ __global__ void __launch_bounds__(32 * kHessRedWarps)
     const int per = (parts + kHessRedWarps - 1) / kHessRedWarps;
     const int q0 = warp * per;
     const int q1 = q0 + per < parts ? q0 + per : parts;
-    double v = 0.0;
-    if (want) {
+    float v = 0.0f;
+    if (want && e > 0) {
+        const float *src = e <= kHMaxP ? part_g + (e - 1) : part_h + (e - 1 - kHMaxP);
+        const size_t stride = e <= kHMaxP ? (size_t)kHMaxP : (size_t)kHMaxP * kHMaxP;
         for (int qb = q0; qb < q1; qb += 16) {
-            double buf[16];
+            float buf[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int q = qb + u;
-                double t = 0.0;
-                if (q < q1) {
-                    if (e == 0)
-                        t = part_f[q];
-                    else if (e <= kHMaxP)
-                        t = (double)part_g[(size_t)q * kHMaxP + e - 1];
-                    else
-                        t = (double)part_h[(size_t)q * kHMaxP * kHMaxP + (e - 1 - kHMaxP)];
-                }
-                buf[u] = t;
-            }
+            for (int u = 0; u < 16; ++u)
+                buf[u] = qb + u < q1 ? __ldg(src + (size_t)(qb + u) * stride) : 0.0f;
 #pragma unroll
             for (int u = 0; u < 16; ++u)
                 v += buf[u];
         }
     }
+    if (blockIdx.x == 0 && lane == 0) {             // f: this warp's CTA range in FP64
+        double fv = 0.0;
+        for (int q = q0; q < q1; ++q)
+            fv += part_f[q];
+        fsum[warp] = fv;
+    }
     sum[warp][lane] = v;
     __syncthreads();
-    if (warp != 0 || !want)
+    if (warp != 0)
         return;
-    double tot = 0.0;
+    float tot = 0.0f;
 #pragma unroll
     for (int w = 0; w < kHessRedWarps; ++w)
         tot += sum[w][lane];
-    if (e == 0) {
-        double bb = 0.0;
-        for (int t = 0; t < P; ++t)
-            bb += (double)beta[t] * (double)beta[t];
-        *f_out = tot - 0.5 * inv_s2 * bb - prior_const;
-    } else if (e <= kHMaxP) {
-        g_out[e - 1] = (float)tot - beta[e - 1] * (float)inv_s2;
+    if (blockIdx.x == 0) {
+        // ||beta||^2 across the warp (P <= 64), then f
+        float bb = 0.0f;
+        for (int t = lane; t < P; t += 32)
+            bb = fmaf(beta[t], beta[t], bb);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            bb += __shfl_xor_sync(0xFFFFFFFFu, bb, o);
+        if (lane == 0) {
+            double ft = 0.0;
+            for (int w = 0; w < kHessRedWarps; ++w)
+                ft += fsum[w];
+            *f_out = ft - 0.5 * inv_s2 * (double)bb - prior_const;
+        }
+    }
+    if (!want || e == 0)
+        return;
+    if (e <= kHMaxP) {
+        g_out[e - 1] = tot - beta[e - 1] * (float)inv_s2;
     } else {
-        const float hv = -(float)tot - (i == j ? (float)inv_s2 : 0.0f);
+        const float hv = -tot - (i == j ? (float)inv_s2 : 0.0f);
         H_out[(size_t)i * P + j] = hv;
         H_out[(size_t)j * P + i] = hv;
     }

@@ -1,9 +1,10 @@
 """GPU parity of the one-pass log-posterior, gradient and Hessian (§4.2's
 derivatives one order further, §5.2) against the FP64 oracle on the same FP32
 X: |f - f_o| / |f_o| <= 1e-5, ||g - g_o|| / ||g_o|| <= 1e-4 and
-||H - H_o||_F / ||H_o||_F <= 1e-4 (FP32 accumulation over up to N / 304 rows
-per partial, then a fixed-order sum). H is exactly symmetric and the result
-bitwise reproducible."""
+||H - H_o||_F / ||H_o||_F <= 1e-4 (the contraction on the tensor cores from
+BF16 hi/lo terms with FP32 accumulation over up to N / 152 rows per partial,
+then a fixed-order FP32 sum of the partials). H is exactly symmetric and the
+result bitwise reproducible."""
 import numpy as np
 import pytest
 
