@@ -8,8 +8,7 @@
 //
 // X^T diag(w) X is a P x P x N contraction and runs on the tcgen05 tensor
 // cores. One persistent CTA per SM streams 128-row tiles of X into shared
-// memory with TMA (128-byte swizzle, a two-tile ring, the tiles beyond the
-// ring prefetched into L2). Eight converter warps (thread = one row and 32
+// memory with TMA (128-byte swizzle, a two-tile ring). Eight converter warps (thread = one row and 32
 // columns) form eta (a partial dot product per half row, exchanged through
 // shared memory), w, r = y - mu and the log-likelihood term, add r x_n to
 // their gradient registers, and write two BF16 operand tiles split into
@@ -49,7 +48,6 @@ constexpr int kHMaxP = 64;
 constexpr int kHConv = 8;                   // converter warps
 constexpr int kHThreads = 32 * (2 + kHConv);
 constexpr int kHStages = 2;                 // X ring (32 KB tiles)
-constexpr int kHL2Ahead = 4;                // tiles prefetched into L2 beyond the ring
 constexpr int kHXTile = kHRows * kHMaxP * 4;
 constexpr int kHAtom = kHRows * 128;        // one 128-byte-wide operand atom (64 bf16)
 constexpr int kHOpBuf = 4 * kHAtom;         // A (two atoms) and B (two atoms)
@@ -71,11 +69,10 @@ __host__ __device__ inline HessLayout hess_layout()
 }
 
 struct HessParams {
-    const float *X;            // L2 prefetch addresses
     const uint8_t *y;
     const float *beta;
     int64_t N;
-    int P, ld;
+    int P;
     double *part_f;
     float *part_g;
     float *part_h;
@@ -151,33 +148,23 @@ __global__ void __launch_bounds__(kHThreads, 1)
     ptx::grid_dep_launch_dependents();
 
     if (warp == 0) {
-        // ---- TMA producer (lane 0) and L2 prefetch of the tiles beyond the ring ----------
-        int pf = kHStages;
-        int okw = 1;
-        const int64_t row_bytes = (int64_t)p.ld * 4;
-        for (int i = 0; i < nt && okw; ++i) {
-            for (; pf < nt && pf < i + kHStages + kHL2Ahead; ++pf) {
-                const int64_t r0p = (int64_t)(b + (int64_t)pf * grid) * kHRows;
-                const int64_t rows = (p.N - r0p) < kHRows ? (p.N - r0p) : kHRows;
-                const uint8_t *base = reinterpret_cast<const uint8_t *>(p.X) + r0p * row_bytes;
-                for (int64_t o = (int64_t)lane * 128; o < rows * row_bytes; o += 32 * 128)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
-            }
-            if (lane == 0) {
+        // ---- TMA producer (lane 0) ---------------------------------------------------------
+        // (Prefetching the tiles beyond the ring into L2 from this warp's
+        // lanes was measured 1 % slower.)
+        if (lane == 0) {
+            for (int i = 0; i < nt; ++i) {
                 const int s = i % kHStages;
                 const int use = i / kHStages;
                 if (use > 0 && !ptx::mbar_wait_bounded(&x_empty[s], (unsigned)(use - 1) & 1u, kSpinLimit)) {
                     atomicOr(p.status, kDevTimeout);
                     s_abort = 1;
-                    okw = 0;
-                } else {
-                    const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kHRows);
-                    ptx::mbar_arrive_expect_tx(&x_full[s], (unsigned)kHXTile);
-                    tc::tma_load_2d(xs + s * kHXTile, &tmap, 0, row0, &x_full[s]);
-                    tc::tma_load_2d(xs + s * kHXTile + kHAtom, &tmap, 32, row0, &x_full[s]);
+                    break;
                 }
+                const int row0 = (int)((int64_t)(b + (int64_t)i * grid) * kHRows);
+                ptx::mbar_arrive_expect_tx(&x_full[s], (unsigned)kHXTile);
+                tc::tma_load_2d(xs + s * kHXTile, &tmap, 0, row0, &x_full[s]);
+                tc::tma_load_2d(xs + s * kHXTile + kHAtom, &tmap, 32, row0, &x_full[s]);
             }
-            okw = __shfl_sync(0xFFFFFFFFu, okw, 0);
         }
     } else if (warp == 1) {
         // ---- MMA issuer: D += A^T B over the tile's 128 rows, 16 per MMA ----------------
@@ -591,12 +578,10 @@ glm_status_t glm_hess_eval(glm_hess_t h, const float *X, const uint8_t *y, const
     }                   // with no rows no tile is loaded and the map is never read
     HessParams p;
     std::memset(&p, 0, sizeof(p));
-    p.X = X;
     p.y = y;
     p.beta = beta;
     p.N = h->n_rows;
     p.P = h->p;
-    p.ld = h->ld;
     p.part_f = h->part_f;
     p.part_g = h->part_g;
     p.part_h = h->part_h;
