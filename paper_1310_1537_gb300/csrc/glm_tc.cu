@@ -54,7 +54,7 @@ struct TcParams {
     int P;
     int kk;                     // vectors in this chunk (<= KB)
     int PA;                     // 64-column atoms of the tile
-    int MB;                     // 128-column blocks of P for MMA2
+    int MB;                     // 128-column blocks of P (row stride of part_g)
     int stages;
     int y_al4;                  // y is 4-byte aligned: labels read as words
     double *part_f;             // grid x 64
@@ -86,9 +86,8 @@ __host__ __device__ constexpr uint32_t idesc_f16kind(int n, int a_mn, int b_mn, 
 // so the logistic needs one more exponential and no reciprocal or select.
 // TR map with the label folded into a sign: z = (1 - 2y) eta, so that
 // ell = -softplus(z) and r = y - sigma(eta) = (2y - 1) sigma(z); ysh holds the
-// label in its sign bit. Adds ell to facc and returns r split into BF16 terms
-// hi = round(r), lo = round(r - hi), packed hi in the low half.
-__device__ __forceinline__ uint32_t tr_pack(float eta, uint32_t ysh, float &facc)
+// label in its sign bit. Adds ell to facc and returns r.
+__device__ __forceinline__ float tr_r(float eta, uint32_t ysh, float &facc)
 {
     constexpr float kLog2e = 1.4426950408889634f;
     constexpr float kLn2 = 0.69314718055994531f;
@@ -98,10 +97,20 @@ __device__ __forceinline__ uint32_t tr_pack(float eta, uint32_t ysh, float &facc
     facc -= fmaxf(z, 0.0f);
     facc = fmaf(-kLn2, L, facc);
     const float sg = ex2_approx(fmaf(fminf(z, 0.0f), kLog2e, -L));   // sigma(z)
-    const float r = __uint_as_float(__float_as_uint(sg) ^ (~ysh & 0x80000000u));
-    const float hi = __bfloat162float(__float2bfloat16_rn(r));
-    __nv_bfloat162 v = __floats2bfloat162_rn(hi, r - hi);
-    return *reinterpret_cast<uint32_t *>(&v);
+    return __uint_as_float(__float_as_uint(sg) ^ (~ysh & 0x80000000u));
+}
+
+// Residuals of two consecutive rows split into BF16 terms hi = round(r),
+// lo = round(r - hi): the hi terms packed in one word and the lo terms in
+// another (row a in the low half).
+__device__ __forceinline__ void split_pair(float ra, float rb, uint32_t &hw, uint32_t &lw)
+{
+    const float ha = __bfloat162float(__float2bfloat16_rn(ra));
+    const float hb = __bfloat162float(__float2bfloat16_rn(rb));
+    __nv_bfloat162 h = __floats2bfloat162_rn(ha, hb);
+    __nv_bfloat162 l = __floats2bfloat162_rn(ra - ha, rb - hb);
+    hw = *reinterpret_cast<uint32_t *>(&h);
+    lw = *reinterpret_cast<uint32_t *>(&l);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr bool FP8 = false;     // BF16 operands (kind::f16, ab_type 1)
     constexpr uint32_t AB = 1u;
     constexpr uint32_t ID1 = tc::idesc_f16kind(128, 0, 0, AB);
-    constexpr uint32_t ID2 = tc::idesc_f16kind(128, 1, 1, AB);
+    const uint32_t ID2 = tc::idesc_f16kind(p.PA * 64, 0, 1, AB);   // N = the tile's columns
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -294,8 +303,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // 256 KB, so no carry): one thread issues every MMA, and its
             // per-MMA work bounds the issue rate
             const uint64_t bk0 = tc::mdesc(ptx::smem_u32(xs), 16, 1024);       // X, K-major
-            const uint64_t am0 = tc::mdesc(ptx::smem_u32(xs), 16384, 1024);    // X, MN-major
-            const uint64_t rm0 = tc::mdesc(ptx::smem_u32(rb), 16384, 1024);    // R, MN-major
+            const uint64_t xm0 = tc::mdesc(ptx::smem_u32(xs), 16384, 1024);    // X, MN-major
+            const uint64_t rt0 = tc::mdesc(ptx::smem_u32(rb), 16, 1024);       // R^t, K-major
             const uint64_t stage_step = (uint64_t)(L.x_stage >> 4);
             bool ok = true;
             for (int i = 0; i <= nt && ok; ++i) {
@@ -325,15 +334,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (!ok)
                         break;
                     tc::fence_after();
-                    const uint64_t ams = am0 + (uint64_t)sj * stage_step;
-                    for (int mb = 0; mb < MB; ++mb) {
-                        const uint64_t adm = ams + (uint64_t)(2 * mb * (16384 >> 4));
-                        const uint32_t dt = tmem + kTcD2Col + mb * 128;
+                    // D2^t[(vector, term) x P] += R^t . X over the tile's rows,
+                    // 16 rows per MMA (R^t atom ks / 4, 32 bytes per step;
+                    // X rows 16 ks: 2 KB per step)
+                    const uint64_t xb = xm0 + (uint64_t)sj * stage_step;
 #pragma unroll
-                        for (int ks = 0; ks < kTcRows / 16; ++ks)     // 16 rows = 2 KB each
-                            tc::mma(dt, adm + (uint64_t)(ks * 128), rm0 + (uint64_t)(ks * 128), ID2,
-                                    (j > 0 || ks > 0) ? 1u : 0u);
-                    }
+                    for (int ks = 0; ks < kTcRows / 16; ++ks)
+                        tc::mma(tmem + kTcD2Col,
+                                rt0 + (uint64_t)((ks >> 2) * (16384 >> 4) + (ks & 3) * 2),
+                                xb + (uint64_t)(ks * 128), ID2, (j > 0 || ks > 0) ? 1u : 0u);
                     tc::commit(&x_empty[sj]);
                     tc::commit(r_empty);
                 }
@@ -364,18 +373,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // shifted so that its low bit is the sign bit
         const uint32_t sh0 = 31u - 16u * (uint32_t)(tr & 1);
         const uint32_t sh1 = sh0 - 8u;
-        // R tile stores: row row_t + 8m + j, columns 2k (hi) and 2k + 1 (lo) of
-        // 64-column region k / 32, with the 128B swizzle of 16-byte chunks by
-        // row & 7 = 2tr + j; conflict-free across the warp
-        uint32_t roff[2][2];
-#pragma unroll
-        for (int g = 0; g < 2; ++g)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const uint32_t chunk = (uint32_t)(4 * (q & 1) + 2 * g + (tq >> 2));
-                roff[g][j] = (uint32_t)((q >> 1) * 16384 + (row_t + j) * 128 + (tq & 3) * 4) +
-                             ((chunk ^ (uint32_t)(2 * tr + j)) << 4);
-            }
+        // R^t tile stores (the A operand of MMA2, K-major: each (vector, term)
+        // lane n holds its 128 rows contiguous, two 64-row atoms of 128 B
+        // rows with the 128B swizzle of 16-byte chunks by n & 7 = tq). The
+        // thread's rows row_t + 8m + {0, 1} of vector 16q + 8g + tq are one
+        // word per term, in lane n = 32q + 16g + 8 term + tq: chunk
+        // (4 (hh & 1) + m) ^ tq, word tr. Conflict-free across the warp.
+        const uint32_t rt_base = (uint32_t)((hh >> 1) * 16384 + (32 * q + tq) * 128 + 4 * tr);
         float facc0 = 0.0f, facc1 = 0.0f;
         uint32_t yw[4], yn[4];
         auto load_y = [&](int i, uint32_t *dst) {
@@ -417,43 +421,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lane == 0)
                 ptx::mbar_arrive(d1_empty);
             const int64_t left = p.N - (int64_t)(b + (int64_t)i * grid) * kTcRows;
-            uint32_t w0[8], w1[8];              // packed (hi, lo) residuals, index 2m + j
+            uint32_t wh[2][4], wl[2][4];        // hi and lo terms of rows (2j pair) per (g, m)
             if (left >= kTcRows) {
 #pragma unroll
-                for (int m = 0; m < 4; ++m)
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const uint32_t ysh = yw[m] << (j ? sh1 : sh0);
-                        w0[2 * m + j] = tc::tr_pack(v0[4 * m + j] + v0[4 * m + 2 + j], ysh, facc0);
-                        w1[2 * m + j] = tc::tr_pack(v1[4 * m + j] + v1[4 * m + 2 + j], ysh, facc1);
-                    }
+                for (int m = 0; m < 4; ++m) {
+                    const uint32_t y0 = yw[m] << sh0, y1 = yw[m] << sh1;
+                    const float a0 = tc::tr_r(v0[4 * m] + v0[4 * m + 2], y0, facc0);
+                    const float a1 = tc::tr_r(v0[4 * m + 1] + v0[4 * m + 3], y1, facc0);
+                    const float b0 = tc::tr_r(v1[4 * m] + v1[4 * m + 2], y0, facc1);
+                    const float b1 = tc::tr_r(v1[4 * m + 1] + v1[4 * m + 3], y1, facc1);
+                    tc::split_pair(a0, a1, wh[0][m], wl[0][m]);
+                    tc::split_pair(b0, b1, wh[1][m], wl[1][m]);
+                }
             } else {
 #pragma unroll
-                for (int m = 0; m < 4; ++m)
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const uint32_t ysh = yw[m] << (j ? sh1 : sh0);
-                        const bool in = row_t + 8 * m + j < left;
-                        float f0 = 0.0f, f1 = 0.0f;
-                        const uint32_t a0 = tc::tr_pack(v0[4 * m + j] + v0[4 * m + 2 + j], ysh, f0);
-                        const uint32_t a1 = tc::tr_pack(v1[4 * m + j] + v1[4 * m + 2 + j], ysh, f1);
-                        w0[2 * m + j] = in ? a0 : 0u;
-                        w1[2 * m + j] = in ? a1 : 0u;
-                        facc0 += in ? f0 : 0.0f;
-                        facc1 += in ? f1 : 0.0f;
-                    }
+                for (int m = 0; m < 4; ++m) {
+                    const uint32_t y0 = yw[m] << sh0, y1 = yw[m] << sh1;
+                    const bool in0 = row_t + 8 * m < left, in1 = row_t + 8 * m + 1 < left;
+                    float f00 = 0.0f, f01 = 0.0f, f10 = 0.0f, f11 = 0.0f;
+                    float a0 = tc::tr_r(v0[4 * m] + v0[4 * m + 2], y0, f00);
+                    float a1 = tc::tr_r(v0[4 * m + 1] + v0[4 * m + 3], y1, f01);
+                    float b0 = tc::tr_r(v1[4 * m] + v1[4 * m + 2], y0, f10);
+                    float b1 = tc::tr_r(v1[4 * m + 1] + v1[4 * m + 3], y1, f11);
+                    a0 = in0 ? a0 : 0.0f;
+                    b0 = in0 ? b0 : 0.0f;
+                    a1 = in1 ? a1 : 0.0f;
+                    b1 = in1 ? b1 : 0.0f;
+                    facc0 += (in0 ? f00 : 0.0f) + (in1 ? f01 : 0.0f);
+                    facc1 += (in0 ? f10 : 0.0f) + (in1 ? f11 : 0.0f);
+                    tc::split_pair(a0, a1, wh[0][m], wl[0][m]);
+                    tc::split_pair(b0, b1, wh[1][m], wl[1][m]);
+                }
             }
             if (i >= 1 && !ptx::mbar_wait_bounded(r_empty, (unsigned)(i - 1) & 1u, kSpinLimit)) {
                 ok = false;
                 break;
             }
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
+            for (int m = 0; m < 4; ++m) {
+                const uint32_t sw = ((uint32_t)((4 * (hh & 1) + m) ^ tq)) << 4;
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    *reinterpret_cast<uint32_t *>(rb + roff[0][j] + m * 1024) = w0[2 * m + j];
-                    *reinterpret_cast<uint32_t *>(rb + roff[1][j] + m * 1024) = w1[2 * m + j];
+                for (int g = 0; g < 2; ++g) {
+                    uint8_t *dst = rb + rt_base + (uint32_t)(16 * g * 128) + sw;
+                    *reinterpret_cast<uint32_t *>(dst) = wh[g][m];              // term hi: lane + 0
+                    *reinterpret_cast<uint32_t *>(dst + 8 * 128) = wl[g][m];    // term lo: lane + 8
                 }
+            }
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0)
@@ -473,20 +486,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             s_abort = 1;
         }
         tc::fence_after();
-        // g partial: D2 block mb, lane = column p of X; this warp's CW/2 vectors
-        for (int mb = 0; mb < MB; ++mb) {
-            float gv[CW];
+        // g partial: D2^t lanes as beta's (hi of vector 16q + 8g + v in lane
+        // 16g + v of quarter q, lo eight lanes further), columns = columns of
+        // X; warp hh takes the 32-column chunks c = hh, hh + 4, and a
+        // 16x256b load gives each thread both terms of its (vector, column)
+        // pairs
+        const int ncol = PA * 64;
+        for (int c = hh; 32 * c < ncol; c += kTcEpiGroups) {
+            float ga[16], gb[16];
             if (have) {
-                tc::tmem_ld<CW>(tmem + ((uint32_t)(q * 32) << 16) + kTcD2Col + mb * 128 + CW * hh, gv);
+                const uint32_t tg = tmem + ((uint32_t)(q * 32) << 16) + kTcD2Col + 32 * c;
+                tc::tmem_ld16x256_x4(tg, ga);
+                tc::tmem_ld16x256_x4(tg + (16u << 16), gb);
                 tc::tmem_wait_ld();
             }
-            const int pcol = mb * 128 + q * 32 + lane;
 #pragma unroll
-            for (int kk2 = 0; kk2 < CW / 2; ++kk2) {
-                const int kv = (CW / 2) * hh + kk2;
-                if (kv < p.kk)
-                    p.part_g[((size_t)b * 64 + kv) * PP + pcol] =
-                        have ? gv[2 * kk2] + gv[2 * kk2 + 1] : 0.0f;
+            for (int g = 0; g < 2; ++g) {
+                const int kv = kq + 8 * g;
+                if (kv >= p.kk)
+                    continue;
+                const float *v = g ? gb : ga;
+                float *dst = p.part_g + ((size_t)b * 64 + kv) * PP + 32 * c + 2 * tr;
+#pragma unroll
+                for (int i2 = 0; i2 < 4; ++i2) {
+                    float2 o;
+                    o.x = have ? v[4 * i2] + v[4 * i2 + 2] : 0.0f;
+                    o.y = have ? v[4 * i2 + 1] + v[4 * i2 + 3] : 0.0f;
+                    *reinterpret_cast<float2 *>(dst + 8 * i2) = o;
+                }
             }
         }
         // f partial: the four lanes of a vector, then the row groups in order
