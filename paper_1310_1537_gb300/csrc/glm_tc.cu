@@ -247,26 +247,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // each epilogue thread both partial sums of one (row, vector) pair, so
     // they add in registers with no exchange between lanes.
     constexpr int EPI0 = 2;                         // first epilogue warp
-    if (warp >= EPI0 && warp < EPI0 + 4) {
+    // All 16 epilogue warps fill it: warp (q, hh) writes the 32-column blocks
+    // cb = 32 hh, 32 (hh + 4), ... of lane quarter q, so each thread has one
+    // batch of loads in flight (a thread's 64 columns are contiguous: 16-byte
+    // loads when the rows allow them).
+    if (warp >= EPI0) {
         const int q = warp & 3;
+        const int hh = (warp - EPI0) >> 2;
         const int k = 16 * q + 8 * (lane >> 4) + (lane & 7);
         const int part = (lane >> 3) & 1;
-        for (int cb = 0; cb < PA * 32; cb += 32) {
+        const bool kin = k < p.kk;
+        const float *brow = p.beta + (size_t)(kin ? k : 0) * p.P;
+        const bool vec = kin && (p.P & 3) == 0 && (reinterpret_cast<uintptr_t>(p.beta) & 15u) == 0;
+        for (int cb = 32 * hh; cb < PA * 32; cb += 32 * kTcEpiGroups) {
+            float v[64];
+            if (vec) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int col = 2 * cb + 4 * u;
+                    float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (col < p.P)
+                        t = __ldg(reinterpret_cast<const float4 *>(brow + col));
+                    v[4 * u] = t.x;
+                    v[4 * u + 1] = t.y;
+                    v[4 * u + 2] = t.z;
+                    v[4 * u + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 64; ++e) {
+                    const int col = 2 * cb + e;
+                    v[e] = (kin && col < p.P) ? __ldg(brow + col) : 0.0f;
+                }
+            }
             uint32_t r[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                float v2[2];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int col = 2 * (cb + j) + e;
-                    float v = 0.0f;
-                    if (k < p.kk && col < p.P)
-                        v = p.beta[(size_t)k * p.P + col];
-                    float hi, lo;
-                    tc::split2<FP8>(v, hi, lo);
-                    v2[e] = part ? lo : hi;
-                }
-                r[j] = tc::pack2<FP8>(v2[0], v2[1]);
+                float h0, l0, h1, l1;
+                tc::split2<FP8>(v[2 * j], h0, l0);
+                tc::split2<FP8>(v[2 * j + 1], h1, l1);
+                r[j] = part ? tc::pack2<FP8>(l0, l1) : tc::pack2<FP8>(h0, h1);
             }
             tc::tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + kTcB1Col + cb, r);
         }
