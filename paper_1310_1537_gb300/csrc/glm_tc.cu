@@ -566,75 +566,94 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // Fixed-order combine of the per-CTA partials, plus the Gaussian prior.
-// g: a block takes 32 consecutive columns of one vector; its 8 warps each add
-// a contiguous range of CTAs (all loads of a range in flight, coalesced over
-// the columns), then warp 0 adds the 8 range sums in order. f: one warp per
-// vector, lanes over CTAs and over columns of beta, finished by a butterfly.
+// The first nf blocks take f: one warp per vector, lanes over CTAs (FP64)
+// and over columns of beta (FP32), finished by a butterfly. The other blocks
+// take g: a block takes 128 consecutive columns of one vector, lane l
+// columns 4l .. 4l + 3 (16-byte loads; the partial rows are padded to a
+// multiple of 128 columns), its 8 warps each add a contiguous range of CTAs
+// with all loads of the range in flight, then warp 0 adds the 8 range sums in
+// order. FP32 sums: FP64 throughput is low on this part, and the partials
+// are FP32 tensor-memory sums already.
 constexpr int kTcRedWarps = 8;
 
 __global__ void __launch_bounds__(32 * kTcRedWarps)
     tc_reduce_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g, int parts,
-                     int KB, int PP, int P, int kk, int ng, const float *__restrict__ beta,
+                     int KB, int PP, int P, int kk, int nf, const float *__restrict__ beta,
                      const float *__restrict__ x_scale, double inv_s2, double prior_const,
                      double *__restrict__ f_out, float *__restrict__ g_out)
 {
     ptx::grid_dep_wait();
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    if ((int)blockIdx.x < ng) {
-        __shared__ float part_sum[kTcRedWarps][32];
-        const int cpk = (P + 31) / 32;                 // column blocks per vector
-        const int k = blockIdx.x / cpk;
-        const int jj = (blockIdx.x - k * cpk) * 32 + lane;
-        const int per = (parts + kTcRedWarps - 1) / kTcRedWarps;
-        const int c0 = warp * per;
-        const int c1 = (c0 + per) < parts ? (c0 + per) : parts;
-        // FP32 sums in a fixed order (FP64 throughput is low on this part;
-        // the partials are FP32 tensor-memory sums already)
-        float v = 0.0f;
-        if (jj < P) {
-            const float *src = part_g + (size_t)k * PP + jj;
-            const size_t stride = (size_t)KB * PP;
-            for (int cb = c0; cb < c1; cb += 32) {
-                float buf[32];
+    if ((int)blockIdx.x < nf) {
+        const int k = (int)blockIdx.x * kTcRedWarps + warp;
+        if (k >= kk)
+            return;
+        double v = 0.0;
+        for (int c = lane; c < parts; c += 32)
+            v += part_f[(size_t)c * KB + k];
+        float bb = 0.0f;
+        for (int t = lane; t < P; t += 32) {
+            const float bt = beta[(size_t)k * P + t];
+            bb = fmaf(bt, bt, bb);
+        }
 #pragma unroll
-                for (int u = 0; u < 32; ++u)
-                    buf[u] = (cb + u < c1) ? __ldg(src + (size_t)(cb + u) * stride) : 0.0f;
+        for (int m = 16; m > 0; m >>= 1) {
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+            bb += __shfl_xor_sync(0xFFFFFFFFu, bb, m);
+        }
+        if (lane == 0)
+            f_out[k] = v - 0.5 * inv_s2 * (double)bb - prior_const;
+        return;
+    }
+    __shared__ float4 part_sum[kTcRedWarps][32];
+    const int gblk = (int)blockIdx.x - nf;
+    const int cpk = (P + 127) / 128;                   // column blocks per vector
+    const int k = gblk / cpk;
+    const int jj = (gblk - k * cpk) * 128 + 4 * lane;
+    const int per = (parts + kTcRedWarps - 1) / kTcRedWarps;
+    const int c0 = warp * per;
+    const int c1 = (c0 + per) < parts ? (c0 + per) : parts;
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (jj < P) {
+        const float *src = part_g + (size_t)k * PP + jj;
+        const size_t stride = (size_t)KB * PP;
+        for (int cb = c0; cb < c1; cb += 16) {
+            float4 buf[16];
 #pragma unroll
-                for (int u = 0; u < 32; ++u)
-                    v += buf[u];
+            for (int u = 0; u < 16; ++u)
+                buf[u] = (cb + u < c1) ? __ldg(reinterpret_cast<const float4 *>(src + (size_t)(cb + u) * stride))
+                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                v.x += buf[u].x;
+                v.y += buf[u].y;
+                v.z += buf[u].z;
+                v.w += buf[u].w;
             }
         }
-        part_sum[warp][lane] = v;
-        __syncthreads();
-        if (warp == 0 && jj < P) {
-            float t = 0.0f;
+    }
+    part_sum[warp][lane] = v;
+    __syncthreads();
+    if (warp != 0 || jj >= P)
+        return;
+    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int w = 0; w < kTcRedWarps; ++w)
-                t += part_sum[w][lane];
-            const float sc = x_scale ? x_scale[jj] : 1.0f;
-            g_out[(size_t)k * P + jj] = fmaf(sc, t, -beta[(size_t)k * P + jj] * (float)inv_s2);
+    for (int w = 0; w < kTcRedWarps; ++w) {
+        const float4 q = part_sum[w][lane];
+        t[0] += q.x;
+        t[1] += q.y;
+        t[2] += q.z;
+        t[3] += q.w;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int col = jj + e;
+        if (col < P) {
+            const float sc = x_scale ? x_scale[col] : 1.0f;
+            g_out[(size_t)k * P + col] = fmaf(sc, t[e], -beta[(size_t)k * P + col] * (float)inv_s2);
         }
-        return;
     }
-    const int k = ((int)blockIdx.x - ng) * kTcRedWarps + warp;
-    if (k >= kk)
-        return;
-    double v = 0.0;
-    for (int c = lane; c < parts; c += 32)
-        v += part_f[(size_t)c * KB + k];
-    double bb = 0.0;
-    for (int t = lane; t < P; t += 32) {
-        const double bt = (double)beta[(size_t)k * P + t];
-        bb += bt * bt;
-    }
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
-        bb += __shfl_xor_sync(0xFFFFFFFFu, bb, m);
-    }
-    if (lane == 0)
-        f_out[k] = v - 0.5 * inv_s2 * bb - prior_const;
 }
 
 // ---------------------------------------------------------------------------
@@ -742,7 +761,7 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         cfg.numAttrs = 1;
         if (cudaLaunchKernelEx(&cfg, fn, *map, prm) != cudaSuccess)
             return GLM_ERR_CUDA;
-        const int ng = kk * ((P + 31) / 32);
+        const int ng = kk * ((P + 127) / 128);
         const int nf = (kk + kTcRedWarps - 1) / kTcRedWarps;
         cudaLaunchConfig_t rc = {};
         rc.gridDim = dim3((unsigned)(ng + nf));
@@ -751,7 +770,7 @@ glm_status_t launch_tc(glm_ctx *h, const void *X, const float *x_scale, const ui
         rc.attrs = attr;
         rc.numAttrs = 1;
         if (cudaLaunchKernelEx(&rc, tc_reduce_kernel, (const double *)h->tc_part_f,
-                               (const float *)h->tc_part_g, h->sm_count, KB, MB * 128, P, kk, ng,
+                               (const float *)h->tc_part_g, h->sm_count, KB, MB * 128, P, kk, nf,
                                beta + (size_t)k0 * P, x_scale, prior ? 1.0 / s2 : 0.0,
                                prior ? 0.5 * (double)P * std::log(2.0 * M_PI * s2) : 0.0, f_out + k0,
                                g_out + (size_t)k0 * P) != cudaSuccess)

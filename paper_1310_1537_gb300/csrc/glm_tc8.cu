@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Fixed-order combine of the per-CTA partials (defined with the BF16 pass).
 __global__ void tc_reduce_kernel(const double *__restrict__ part_f, const float *__restrict__ part_g,
-                                 int parts, int KB, int PP, int P, int kk, int ng,
+                                 int parts, int KB, int PP, int P, int kk, int nf,
                                  const float *__restrict__ beta, const float *__restrict__ x_scale,
                                  double inv_s2, double prior_const, double *__restrict__ f_out,
                                  float *__restrict__ g_out);
@@ -722,7 +722,7 @@ glm_status_t launch_tc8(glm_ctx *h, const void *X, const float *x_scale, const u
         cfg.numAttrs = 1;
         if (cudaLaunchKernelEx(&cfg, tc8_logpost_grad_kernel, *map, prm) != cudaSuccess)
             return GLM_ERR_CUDA;
-        const int ng = kk * ((P + 31) / 32);
+        const int ng = kk * ((P + 127) / 128);
         const int nf = (kk + kTc8RedWarps - 1) / kTc8RedWarps;
         cudaLaunchConfig_t rc = {};
         rc.gridDim = dim3((unsigned)(ng + nf));
@@ -731,7 +731,7 @@ glm_status_t launch_tc8(glm_ctx *h, const void *X, const float *x_scale, const u
         rc.attrs = attr;
         rc.numAttrs = 1;
         if (cudaLaunchKernelEx(&rc, tc_reduce_kernel, (const double *)h->tc_part_f,
-                               (const float *)h->tc_part_g, h->sm_count, kVec, PP, P, kk, ng,
+                               (const float *)h->tc_part_g, h->sm_count, kVec, PP, P, kk, nf,
                                beta + (size_t)k0 * P, x_scale, prior ? 1.0 / s2 : 0.0,
                                prior ? 0.5 * (double)P * std::log(2.0 * M_PI * s2) : 0.0,
                                f_out + k0, g_out + (size_t)k0 * P) != cudaSuccess)
