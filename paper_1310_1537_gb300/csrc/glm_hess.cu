@@ -211,11 +211,18 @@ __global__ void __launch_bounds__(kHThreads, 1)
         }
         float facc = 0.0f;
         bool ok = true;
+        // labels one tile ahead
+        auto label = [&](int i) -> int {
+            const int64_t rw = (int64_t)(b + (int64_t)i * grid) * kHRows + r;
+            return (i < nt && rw < p.N) ? (int)__ldg(p.y + rw) : 0;
+        };
+        int ynext = label(0);
         for (int i = 0; i < nt; ++i) {
             const int s = i % kHStages;
             const int64_t row = (int64_t)(b + (int64_t)i * grid) * kHRows + r;
             const bool valid = row < p.N;
-            const int yl = valid ? (int)__ldg(p.y + row) : 0;
+            const int yl = ynext;
+            ynext = label(i + 1);
             if (!ptx::mbar_wait_bounded(&x_full[s], (unsigned)(i / kHStages) & 1u, kSpinLimit)) {
                 ok = false;
                 break;
@@ -237,10 +244,12 @@ __global__ void __launch_bounds__(kHThreads, 1)
                 for (int j = 0; j < 32; ++j)
                     x[j] = 32 * hf + j < p.P ? x[j] : 0.0f;
             }
-            float part = 0.0f;
+            // four independent chains (a shorter dependency than one of 32)
+            float pc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                part = fmaf(x[j], bt[j], part);
+                pc[j & 3] = fmaf(x[j], bt[j], pc[j & 3]);
+            const float part = (pc[0] + pc[1]) + (pc[2] + pc[3]);
             // exchange the half-row sums (buffer and barrier by tile parity: no
             // warp can be two tiles ahead, as every tile needs all eight)
             float *epb = ep + (i & 1) * 2 * kHRows;
