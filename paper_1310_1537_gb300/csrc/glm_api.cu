@@ -128,7 +128,10 @@ glm_status_t fused_configure(glm_ctx *h)
     }
     h->fx_map_ptr = nullptr;
     h->smem_bytes = fused_smem_total(h, T, stages, h->kc_max, srow);
-    h->grid = h->sm_count;
+    // one CTA per SM, but no more CTAs than tiles of rows: for small N the
+    // extra CTAs would only add to the cross-CTA combine and the ticket
+    const int64_t tiles = (h->d.n_rows + T - 1) / T;
+    h->grid = tiles < (int64_t)h->sm_count ? (tiles > 0 ? (int)tiles : 1) : h->sm_count;
     h->use_pdl = 1;
     return GLM_OK;
 }
