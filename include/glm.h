@@ -142,7 +142,11 @@ GLM_API glm_status_t glm_get_info(glm_handle_t h, glm_info_t *info);
  * f is accumulated per row in FP32 and across CTAs in FP64; g is accumulated
  * in FP32 and combined across CTAs in FP64. Results are deterministic: the
  * same inputs give bitwise the same outputs, whatever else runs. K >= tc_min_k
- * with BF16/FP8 storage runs on the tcgen05 tensor cores (see glm_get_info).
+ * with BF16/FP8 storage and p <= 256 runs on the tcgen05 tensor cores (see
+ * glm_get_info): there the coefficients and residuals enter the MMAs as sums
+ * of terms of X's type (two BF16 terms; four and five E4M3 terms), the MMAs
+ * accumulate in FP32, and the per-CTA partials of g are added in a fixed
+ * order in FP32 (f in FP64).
  */
 GLM_API glm_status_t glm_logpost_grad(glm_handle_t h, const void *X, const float *x_scale,
                               const uint8_t *y, const float *beta, int32_t K,
