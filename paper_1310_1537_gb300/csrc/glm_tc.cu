@@ -4,27 +4,31 @@
 // (§4.2: X beta, then X^t g_f) become real contractions, N x P x K each. One
 // persistent CTA per SM streams 128-row tiles of X (BF16) into shared memory
 // with TMA (128B swizzle, 2-4 stages) and, from the same staged tile,
-//   MMA1: D1[2K x 128] = B1 . X_tile^T   (A = B1 in tensor memory: rows 2k and
-//         2k+1 hold the bf16 hi and lo parts of beta_k; B = the tile, K-major)
-//   epilogue (16 warps): lane n of D1 belongs to vector k = n/2; the two
-//         lanes of a vector add their hi and lo products (one shuffle) to get
-//         eta for 32 rows, each takes 16 of them through the TR map (ell, r),
-//         accumulates f, splits r into bf16 hi + lo and writes them to the
-//         R tile in shared memory
-//   MMA2: D2[P x 2K] += X_tile^T . R_tile   (both operands MN-major)
-// D2 stays in tensor memory for the CTA's whole run: the gradient never
-// leaves the SM until the end. Splitting beta and r into two bf16 terms keeps
-// about 16 significant bits, so the results match the FP32 path to ~1e-5
-// while X stays in 2-byte storage. Per-CTA partials are combined by a second
-// kernel in a fixed order (deterministic).
+//   MMA1: D1[128 lanes x 128 rows] = B1 . X_tile^T, with A = B1 in tensor
+//         memory (lanes in groups of 16: lane 16g + v holds the bf16 hi part
+//         of beta for vector 16q + 8g + v of lane quarter q, the lo part
+//         eight lanes further) and B = the tile, K-major;
+//   epilogue (16 warps): 16x256b tensor-memory loads give each thread the hi
+//         and lo partial sums of its (row, vector) pairs, which add to eta;
+//         the TR map (labels folded in as a sign) gives ell and r; f is
+//         accumulated per thread, and r is split into bf16 hi + lo and
+//         written transposed (lane = vector and term, rows contiguous) into
+//         the residual tile in shared memory;
+//   MMA2: D2^t[128 lanes x P] += R^t . X_tile, with A = the residual tile
+//         (K-major) and B = the X tile read MN-major, N = the tile's columns.
+// D2^t stays in tensor memory for the CTA's whole run: the gradient never
+// leaves the SM until the end, when the hi and lo lanes are added. Splitting
+// beta and r into two bf16 terms keeps about 16 significant bits, so the
+// results match the FP32 path to ~1e-5 while X stays in 2-byte storage.
+// Per-CTA partials are combined by a second kernel in a fixed order
+// (deterministic).
 //
 // FP8 E4M3 storage has its own pass (glm_tc8.cu), which takes the E4M3
 // operands directly.
 //
 // Warp roles: warp 0 issues TMA loads, warp 1 allocates tensor memory and one
-// of its threads issues the MMAs, warps 2..17 first load beta into tensor
-// memory and then run the epilogue.
-// Every wait is bounded.
+// of its threads issues the MMAs, warps 2..17 first write beta into tensor
+// memory and then run the epilogue. Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -63,13 +67,6 @@ struct TcParams {
 };
 
 namespace tc {
-
-__device__ __forceinline__ uint32_t sw128(int r, int c_elem16)
-{
-    // byte offset of 16-bit element (r, c) in a [rows x 64] region, 128B swizzle
-    const uint32_t chunk = (uint32_t)c_elem16 >> 3;
-    return (uint32_t)r * 128u + ((chunk ^ ((uint32_t)r & 7u)) << 4) + (((uint32_t)c_elem16 & 7u) << 1);
-}
 
 // kind::f16 instruction descriptor: D f32, A and B both bf16 (ab_type 1) or
 // both f16 (ab_type 0), M=128, N=n.
@@ -119,33 +116,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-__device__ __forceinline__ uint32_t pack_f16(float a, float b)
-{
-    __half2 v = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&v);
-}
-
-// Two-term split of v in the operand type: hi = round(v), lo = round(v - hi).
-template <bool F16>
+// Two-term split of v in BF16: hi = round(v), lo = v - hi (rounded when packed).
 __device__ __forceinline__ void split2(float v, float &hi, float &lo)
 {
-    if constexpr (F16) {
-        hi = __half2float(__float2half_rn(v));
-    } else {
-        hi = __bfloat162float(__float2bfloat16_rn(v));
-    }
+    hi = __bfloat162float(__float2bfloat16_rn(v));
     lo = v - hi;
 }
-
-template <bool F16>
-__device__ __forceinline__ uint32_t pack2(float a, float b)
-{
-    if constexpr (F16)
-        return pack_f16(a, b);
-    else
-        return pack_bf16(a, b);
-}
-
 
 }  // namespace tc
 
@@ -153,9 +129,9 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
 struct TcLayout {
     int x_stage;    // PA * 16 KB (bf16 / f16 operand tile, 128B swizzle)
     int x_off;
-    int r_off;      // R tile: 2 regions of (128 rows x 128 B)
+    int r_off;      // residual tile R^t: 2 atoms of (128 lanes x 128 B), K-major
     int bar_off;    // barriers, tensor-memory slot, per-vector scales
-    int sf_off;     // 4 x 64 doubles (inside the R tile, used after the last MMA)
+    int sf_off;     // 4 x 64 doubles (inside the residual tile, used after the last MMA)
     int total;      // including 1 KB alignment slack
 };
 
@@ -180,7 +156,6 @@ constexpr int kTcD2Col = 256;
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_logpost_grad_kernel(const __grid_constant__ CUtensorMap tmap, TcParams p)
 {
-    constexpr bool FP8 = false;     // BF16 operands (kind::f16, ab_type 1)
     constexpr uint32_t AB = 1u;
     constexpr uint32_t ID1 = tc::idesc_f16kind(128, 0, 0, AB);
     const uint32_t ID2 = tc::idesc_f16kind(p.PA * 64, 0, 1, AB);   // N = the tile's columns
@@ -284,9 +259,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 float h0, l0, h1, l1;
-                tc::split2<FP8>(v[2 * j], h0, l0);
-                tc::split2<FP8>(v[2 * j + 1], h1, l1);
-                r[j] = part ? tc::pack2<FP8>(l0, l1) : tc::pack2<FP8>(h0, h1);
+                tc::split2(v[2 * j], h0, l0);
+                tc::split2(v[2 * j + 1], h1, l1);
+                r[j] = part ? tc::pack_bf16(l0, l1) : tc::pack_bf16(h0, h1);
             }
             tc::tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + kTcB1Col + cb, r);
         }
