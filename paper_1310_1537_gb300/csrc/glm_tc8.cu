@@ -28,9 +28,10 @@
 // terms (block A, scale 2^8); the FP32 remainder (v - a16) 2^12 is rounded to
 // FP16 and split into two more (block B, scale 2^20).
 //
-// Warp roles: warp 0 issues the TMA loads, warp 1 owns tensor memory and one
-// of its threads issues the MMAs, warps 2..17 write the coefficient terms into
-// shared memory and then run the epilogue. Every wait is bounded.
+// Warp roles: all ten warps first stage the coefficients and write their
+// E4M3 terms into shared memory; then warp 0 issues the TMA loads, warp 1
+// owns tensor memory and one of its threads issues the MMAs, and warps 2..9
+// run the epilogue. Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -256,11 +257,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     {
         const int nb = p.kk * p.P;
         if ((reinterpret_cast<uintptr_t>(p.beta) & 15u) == 0 && (nb & 3) == 0) {
+            // batches of eight independent 16-byte loads per thread
             const float4 *src = reinterpret_cast<const float4 *>(p.beta);
             float4 *dst = reinterpret_cast<float4 *>(bst);
-#pragma unroll 4
-            for (int idx = tid; idx < nb / 4; idx += kThreads)
-                dst[idx] = __ldg(src + idx);
+            const int n4 = nb / 4;
+            for (int base = tid; base < n4; base += 8 * kThreads) {
+                float4 t[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int idx = base + u * kThreads;
+                    t[u] = idx < n4 ? __ldg(src + idx) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int idx = base + u * kThreads;
+                    if (idx < n4)
+                        dst[idx] = t[u];
+                }
+            }
         } else {
 #pragma unroll 4
             for (int idx = tid; idx < nb; idx += kThreads)
