@@ -69,7 +69,11 @@ __device__ void group_finalize(const GroupedParams &p, int g, bool from_acc, int
     }
 }
 
-template <typename Tag>
+// PCX > 0: rows of exactly PCX 16-byte chunks, all of them holding used
+// columns (ld * element size = 16 PCX, ceil(P / EPC) = PCX), so that the row
+// stride, the chunk rotation and the lane mapping are compile-time constants;
+// PCX = 0 takes them from the parameters.
+template <typename Tag, int PCX>
 __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_kernel(GroupedParams p)
 {
     using TR = XTraits<Tag>;
@@ -77,6 +81,8 @@ __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_ke
     constexpr int ES = TR::ES;
     constexpr unsigned FULL = 0xFFFFFFFFu;
     constexpr int CR = kGroupedRows;
+    static_assert((PCX & (PCX - 1)) == 0, "PCX is 0 or a power of two");
+    constexpr int kU1 = PCX ? PCX : 4;
 
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x;
@@ -87,9 +93,9 @@ __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_ke
     const int grid = gridDim.x;
     const int P = p.P;
     const int ld = p.ld;
-    const int PC = ld / EPC;
-    const int PCU = (P + EPC - 1) / EPC;
-    const int row_bytes = ld * ES;
+    const int PC = PCX ? PCX : ld / EPC;
+    const int PCU = PCX ? PCX : (P + EPC - 1) / EPC;
+    const int row_bytes = PCX ? 16 * PCX : ld * ES;
     const int G = p.G;
     const int stages = p.stages;
     const int slot_bytes = CR * row_bytes;
@@ -332,9 +338,9 @@ __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_ke
             float eta = 0.0f;
             int cs = rot;
             if (uniform) {
-#pragma unroll 4
+#pragma unroll kU1
                 for (int it = 0; it < PCU; ++it) {
-                    const int c = cs;
+                    const int c = PCX ? ((rot + it) & (PCX - 1)) : cs;
                     cs = (cs + 1 == PCU) ? 0 : cs + 1;
                     float xv[EPC];
                     TR::load(xr + c * 16, xv);
@@ -384,17 +390,32 @@ __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_ke
             }
             const int64_t gend = cur_end;
             const int e_end = (int)((gend - row0) < nrows ? (gend - row0) : nrows);
-#pragma unroll 2
-            for (int i0 = sidx; i0 < e_end; i0 += RS) {
-                const int ii = i0 + rs;
-                const bool v2 = ii < e_end;
-                const float ri = __shfl_sync(FULL, r, v2 ? ii : 0);
-                if (v2 && ch < PCU) {
+            if (PCX && sidx == 0 && e_end == CR) {
+                // a whole slot of one group: the same steps, fully unrolled,
+                // with the row offsets as constants
+                const uint8_t *xb = slot + rs * row_bytes + ch * 16;
+#pragma unroll
+                for (int i0 = 0; i0 < CR; i0 += RS) {
+                    const float ri = __shfl_sync(FULL, r, i0 + rs);
                     float xv[EPC];
-                    TR::load(slot + ii * row_bytes + ch * 16, xv);
+                    TR::load(xb + i0 * row_bytes, xv);
 #pragma unroll
                     for (int e = 0; e < EPC; ++e)
                         gacc[e] = fmaf(ri, xv[e], gacc[e]);
+                }
+            } else {
+#pragma unroll 2
+                for (int i0 = sidx; i0 < e_end; i0 += RS) {
+                    const int ii = i0 + rs;
+                    const bool v2 = ii < e_end;
+                    const float ri = __shfl_sync(FULL, r, v2 ? ii : 0);
+                    if (v2 && ch < PCU) {
+                        float xv[EPC];
+                        TR::load(slot + ii * row_bytes + ch * 16, xv);
+#pragma unroll
+                        for (int e = 0; e < EPC; ++e)
+                            gacc[e] = fmaf(ri, xv[e], gacc[e]);
+                    }
                 }
             }
             if (lane >= sidx && lane < e_end)
@@ -869,10 +890,12 @@ glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, con
                                   ((h->d.p + epc - 1) / epc) * epc, nchunks > 0, h->gr_units);
     void (*fn)(GroupedParams) = nullptr;
     const bool narrow = nchunks > 0 && h->gr_narrow;
+    // rows of exactly eight 16-byte chunks, all holding used columns
+    const bool rows8 = h->d.ld * h->elem_bytes == 128 && (h->d.p + epc - 1) / epc == 8;
     switch (h->d.xtype) {
     case GLM_X_F32:
         if (!narrow)
-            fn = grouped_logpost_grad_kernel<F32Tag>;
+            fn = rows8 ? grouped_logpost_grad_kernel<F32Tag, 8> : grouped_logpost_grad_kernel<F32Tag, 0>;
         else if (nchunks == 1)
             fn = grouped_narrow_kernel<F32Tag, 1>;
         else if (nchunks == 2)
@@ -884,7 +907,7 @@ glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, con
         break;
     case GLM_X_BF16:
         if (!narrow)
-            fn = grouped_logpost_grad_kernel<BF16Tag>;
+            fn = rows8 ? grouped_logpost_grad_kernel<BF16Tag, 8> : grouped_logpost_grad_kernel<BF16Tag, 0>;
         else if (nchunks == 1)
             fn = grouped_narrow_kernel<BF16Tag, 1>;
         else if (nchunks == 2)
@@ -894,7 +917,7 @@ glm_status_t launch_grouped(glm_ctx *h, const void *X, const float *x_scale, con
         break;
     case GLM_X_FP8E4M3:
         if (!narrow)
-            fn = grouped_logpost_grad_kernel<FP8Tag>;
+            fn = rows8 ? grouped_logpost_grad_kernel<FP8Tag, 8> : grouped_logpost_grad_kernel<FP8Tag, 0>;
         else if (nchunks == 1)
             fn = grouped_narrow_kernel<FP8Tag, 1>;
         else
