@@ -206,6 +206,32 @@ GLM_API glm_status_t glm_autotune_grouped(glm_handle_t h, const void *X, const f
                                           glm_stream_t stream);
 
 /*
+ * glm_grouped_set_shape / glm_grouped_get_shape — the grouped pass's launch
+ * shape, set explicitly (for a reproducible configuration without timing) or
+ * read back (after glm_autotune_grouped):
+ *   variant      0: the warp-stream kernel (lanes split a slot's rows for the
+ *                gradient, any P); 1: the narrow-row kernel (each lane keeps
+ *                its row, the group's coefficients and the gradient sums in
+ *                registers; only when the used columns fit 32 per row)
+ *   warps        warps per CTA: 4, 8, 12 or 16 (at most 12 for variant 1)
+ *   units        32-row units per copy slot: 1, or 2 or 4 with variant 1
+ *   stages       copy slots per warp ring, 2..4
+ *   ctas_per_sm  1 or 2 (the grid is that many CTAs per SM)
+ * These are the shapes glm_autotune_grouped chooses from. Set returns
+ * GLM_ERR_INVALID_ARG for a value outside these ranges or a variant that does
+ * not apply to the handle's P, GLM_ERR_UNSUPPORTED if the shape's shared
+ * memory does not fit, and GLM_ERR_UNSUPPORTED for a handle created without
+ * grouped support (g_max = 0); on an error the shape is unchanged. Get writes
+ * each non-null pointer. Neither call touches the device; do not call them
+ * while another thread launches on the same handle.
+ */
+GLM_API glm_status_t glm_grouped_set_shape(glm_handle_t h, int32_t variant, int32_t warps,
+                                           int32_t units, int32_t stages, int32_t ctas_per_sm);
+GLM_API glm_status_t glm_grouped_get_shape(glm_handle_t h, int32_t *variant, int32_t *warps,
+                                           int32_t *units, int32_t *stages,
+                                           int32_t *ctas_per_sm);
+
+/*
  * glm_rwm_run — K independent random-walk Metropolis chains (the sampler of
  * §2.2 that consumes the log-posterior), n_steps steps each, entirely on the
  * device: step t proposes beta'_k = fmaf(step, z[t][k], beta_k) in FP32,

@@ -42,7 +42,8 @@ EXPORTS = (
     "glm_create", "glm_destroy", "glm_status_str", "glm_get_info", "glm_logpost_grad",
     "glm_logpost_grad_host", "glm_logpost_grad_grouped", "glm_rwm_run", "glm_quantize",
     "glm_sync", "glm_selftest_wait_timeout", "glm_logpost_grad_noalloc",
-    "glm_autotune_grouped", "glm_server_create", "glm_server_add_dataset", "glm_server_submit",
+    "glm_autotune_grouped", "glm_grouped_set_shape", "glm_grouped_get_shape",
+    "glm_server_create", "glm_server_add_dataset", "glm_server_submit",
     "glm_server_poll", "glm_server_wait", "glm_server_stats", "glm_server_destroy",
     "glm_server_remove_dataset",
     "glm_slice_create", "glm_slice_destroy", "glm_slice_eta", "glm_slice_coord_logpost",
@@ -133,6 +134,9 @@ def load(build_if_missing: bool = True):
                                           C.c_double, vp, C.c_int32, vp, vp, vp], st),
             "glm_autotune_grouped": ([vp, vp, vp, vp, vp, C.c_int32, vp, vp, C.c_double, vp, vp,
                                       C.c_int32, vp], st),
+            "glm_grouped_set_shape": ([vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_int32], st),
+            "glm_grouped_get_shape": ([vp] + [C.POINTER(C.c_int32)] * 5, st),
             "glm_server_create": ([C.POINTER(glm_server_desc_t), C.POINTER(vp)], st),
             "glm_server_add_dataset": ([vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_int32,
                                         C.c_int32, C.c_double, C.POINTER(C.c_int32)], st),
@@ -245,6 +249,18 @@ def glm_autotune_grouped(h, X, x_scale, y, group_off, G, beta, mu, tau, f_out, g
                                        int(G), _ptr(beta), _ptr(mu), float(tau), _ptr(f_out),
                                        _ptr(g_out), int(reps), _stream(stream)),
            "glm_autotune_grouped")
+
+
+def glm_grouped_set_shape(h, variant, warps, units, stages, ctas_per_sm) -> None:
+    _check(load().glm_grouped_set_shape(h, int(variant), int(warps), int(units), int(stages),
+                                        int(ctas_per_sm)), "glm_grouped_set_shape")
+
+
+def glm_grouped_get_shape(h) -> tuple:
+    """(variant, warps, units, stages, ctas_per_sm) of the grouped launch."""
+    vals = [C.c_int32() for _ in range(5)]
+    _check(load().glm_grouped_get_shape(h, *[C.byref(v) for v in vals]), "glm_grouped_get_shape")
+    return tuple(v.value for v in vals)
 
 
 def glm_rwm_run(h, X, x_scale, y, K, n_steps, step, z, log_u, beta_state, f_state, init_f,

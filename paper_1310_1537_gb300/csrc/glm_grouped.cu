@@ -468,6 +468,7 @@ __global__ void __launch_bounds__(kNarrowMaxThreads, 1)
     const int grid = gridDim.x;
     const int P = p.P;
     const int row_bytes = p.ld * ES;
+    const int PCS = row_bytes / 16;            // 16-byte chunks per stored row
     const int G = p.G;
     const int stages = p.stages;
     const int U = p.units;                     // 32-row units per TMA slot
@@ -718,7 +719,9 @@ __global__ void __launch_bounds__(kNarrowMaxThreads, 1)
             float ell = 0.0f, r = 0.0f;
     #pragma unroll
             for (int c = 0; c < NCH; ++c) {
-                if (valid) {
+                // chunks past the stored row (NCH rounds its chunk count up
+                // to a power of two) hold no column of this row: zero
+                if (valid && ((c + rot) & (NCH - 1)) < PCS) {
                     TR::load(xrow + ((c + rot) & (NCH - 1)) * 16, xv[c]);
                 } else {
     #pragma unroll
@@ -1022,3 +1025,58 @@ glm_status_t autotune_grouped(glm_ctx *h, const void *X, const float *x_scale, c
 }
 
 }  // namespace glm
+
+// Explicit launch shapes: the autotuner's candidate space, validated the same
+// way (variant, warps per CTA, units per slot, ring slots, CTAs per SM).
+extern "C" glm_status_t glm_grouped_set_shape(glm_handle_t h, int32_t variant, int32_t warps,
+                                              int32_t units, int32_t stages, int32_t ctas_per_sm)
+{
+    using namespace glm;
+    if (!h)
+        return GLM_ERR_INVALID_ARG;
+    if (!h->gr_acc || h->gr_warps == 0)
+        return GLM_ERR_UNSUPPORTED;
+    const int es = h->elem_bytes;
+    const int epc = 16 / es;
+    const int pcue = ((h->d.p + epc - 1) / epc) * epc;
+    const bool narrow_ok = grouped_nch(h->d.p, epc) > 0;
+    if (variant < 0 || variant > 1 || (variant == 1 && !narrow_ok))
+        return GLM_ERR_INVALID_ARG;
+    const int wmax = (variant ? kNarrowMaxThreads : kGroupedMaxThreads) / 32;
+    if ((warps != 4 && warps != 8 && warps != 12 && warps != 16) || warps > wmax)
+        return GLM_ERR_INVALID_ARG;
+    if (units != 1 && !(variant == 1 && (units == 2 || units == 4)))
+        return GLM_ERR_INVALID_ARG;
+    if (stages < 2 || stages > 4 || ctas_per_sm < 1 || ctas_per_sm > 2)
+        return GLM_ERR_INVALID_ARG;
+    const int budget = kSmemOptinBytes / ctas_per_sm - (ctas_per_sm > 1 ? 1024 : 0);
+    if (grouped_smem(h->d.ld * es, warps, stages, pcue, variant, units) > budget)
+        return GLM_ERR_UNSUPPORTED;
+    h->gr_narrow = variant;
+    h->gr_warps = warps;
+    h->gr_units = units;
+    h->gr_stages = stages;
+    h->gr_grid = h->sm_count * ctas_per_sm;
+    return GLM_OK;
+}
+
+extern "C" glm_status_t glm_grouped_get_shape(glm_handle_t h, int32_t *variant, int32_t *warps,
+                                              int32_t *units, int32_t *stages,
+                                              int32_t *ctas_per_sm)
+{
+    if (!h)
+        return GLM_ERR_INVALID_ARG;
+    if (!h->gr_acc || h->gr_warps == 0)
+        return GLM_ERR_UNSUPPORTED;
+    if (variant)
+        *variant = h->gr_narrow;
+    if (warps)
+        *warps = h->gr_warps;
+    if (units)
+        *units = h->gr_units;
+    if (stages)
+        *stages = h->gr_stages;
+    if (ctas_per_sm)
+        *ctas_per_sm = h->sm_count > 0 ? h->gr_grid / h->sm_count : 0;
+    return GLM_OK;
+}

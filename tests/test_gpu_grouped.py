@@ -15,12 +15,15 @@ pytestmark = pytest.mark.gpu
 
 
 def _run_grouped(Xs, y, off, beta, mu, tau, p, xtype=glm.GLM_X_F32, x_scale=None, repeat=1,
-                 n_rows=None):
+                 n_rows=None, shape=None):
     t = torch()
     n, ld = Xs.shape
     G = len(off) - 1
     h = glm.glm_create(n if n_rows is None else n_rows, p, ld, 1, xtype, 10.0, 0, 0, G)
     try:
+        if shape is not None:
+            glm.glm_grouped_set_shape(h, *shape)
+            assert glm.glm_grouped_get_shape(h) == tuple(shape)
         Xd = to_dev(Xs) if n > 0 else t.empty(16, dtype=t.uint8, device="cuda")
         yd = to_dev(y) if n > 0 else t.empty(16, dtype=t.uint8, device="cuda")
         od = to_dev(np.asarray(off, dtype=np.int64))
@@ -194,21 +197,74 @@ def test_grouped_autotuner_keeps_results_correct():
         glm.glm_destroy(h)
 
 
-@pytest.mark.parametrize("narrow", ["0", "1"])
-def test_grouped_both_kernel_variants(narrow, monkeypatch):
-    """The warp-stream kernel and the narrow-row kernel (forced through the
-    environment) on ragged, empty and single-row groups and several row
-    widths."""
-    monkeypatch.setenv("GLM_GROUPED_NARROW", narrow)
+def _shape_smem(shape, p, ld, elem_bytes=4):
+    """Dynamic shared memory of a grouped launch shape (the library's sizing:
+    each warp's ring of slots, its barriers, and the coefficient slice or the
+    narrow kernel's transpose buffer)."""
+    variant, warps, units, stages, _ = shape
+    epc = 16 // elem_bytes
+    pcue = -(-p // epc) * epc
+    ring = -(-(stages * units * 32 * ld * elem_bytes) // 128) * 128
+    extra = 64 + warps * 32 * 17 * 4 if variant else warps * pcue * 4
+    return warps * ring + warps * stages * 8 + extra + 64
+
+
+def _shape_fits(shape, p, ld):
+    ctas = shape[4]
+    return _shape_smem(shape, p, ld) <= 232448 // ctas - (1024 if ctas > 1 else 0)
+
+
+@pytest.mark.parametrize("shape", [(0, 4, 1, 2, 1), (0, 16, 1, 3, 1), (0, 8, 1, 3, 2),
+                                   (1, 4, 1, 2, 1), (1, 12, 2, 2, 1), (1, 4, 4, 2, 1),
+                                   (1, 4, 2, 2, 2)])
+def test_grouped_both_kernel_variants(shape):
+    """The warp-stream kernel (variant 0) and the narrow-row kernel (variant
+    1), set explicitly through glm_grouped_set_shape, on ragged, empty and
+    single-row groups and several row widths: P = 8 and 20 (rows of 2 and 5
+    chunks), 32 (the 128-byte-row instance) and 100 (variant 1 does not apply
+    and is refused; a shape whose rings do not fit in shared memory is
+    refused as unsupported)."""
     sizes = np.array([20, 0, 1, 57, 3000, 33, 0, 512, 31, 32, 64, 1, 2, 4000, 777])
-    for p in (8, 32, 100):
+    for p in (8, 20, 32, 100):
         gd = synth.make_grouped(len(sizes), p, 3 + p, dtype=np.float32, sizes=sizes)
         ld = synth.padded_ld(p, 4)
         Xs = synth.pad_columns(gd.X, ld)
-        (f, g), = _run_grouped(Xs, gd.y, gd.offsets, gd.beta, gd.mu, gd.tau, p)
+        if shape[0] == 1 and p > 32:
+            with pytest.raises(glm.GLMError) as e:
+                _run_grouped(Xs, gd.y, gd.offsets, gd.beta, gd.mu, gd.tau, p, shape=shape)
+            assert e.value.status == glm.GLM_ERR_INVALID_ARG
+            continue
+        if not _shape_fits(shape, p, ld):
+            with pytest.raises(glm.GLMError) as e:
+                _run_grouped(Xs, gd.y, gd.offsets, gd.beta, gd.mu, gd.tau, p, shape=shape)
+            assert e.value.status == glm.GLM_ERR_UNSUPPORTED
+            continue
+        outs = _run_grouped(Xs, gd.y, gd.offsets, gd.beta, gd.mu, gd.tau, p, shape=shape,
+                            repeat=2)
+        np.testing.assert_array_equal(outs[0][0], outs[1][0])
+        np.testing.assert_array_equal(outs[0][1], outs[1][1])
         f_o, g_o = _oracle_grouped(Xs.astype(np.float64), gd.y, gd.offsets,
                                    gd.beta.astype(np.float32), gd.mu.astype(np.float32), gd.tau, p)
-        assert_close(f, g, f_o, g_o, what=f"variant narrow={narrow} P={p}")
+        assert_close(outs[0][0], outs[0][1], f_o, g_o, what=f"shape {shape} P={p}")
+
+
+def test_grouped_shape_setter_rejects_bad_shapes():
+    gd = synth.make_grouped(3, 32, 5, dtype=np.float32, sizes=np.array([10, 10, 10]))
+    h = glm.glm_create(gd.X.shape[0], 32, 32, 1, glm.GLM_X_F32, 10.0, 0, 0, 3)
+    try:
+        before = glm.glm_grouped_get_shape(h)
+        for bad in [(2, 8, 1, 2, 1), (0, 5, 1, 2, 1), (0, 20, 1, 2, 1), (1, 16, 1, 2, 1),
+                    (0, 8, 2, 2, 1), (0, 8, 1, 1, 1), (0, 8, 1, 5, 1), (0, 8, 1, 2, 3)]:
+            with pytest.raises(glm.GLMError) as e:
+                glm.glm_grouped_set_shape(h, *bad)
+            assert e.value.status == glm.GLM_ERR_INVALID_ARG, bad
+        # 16 warps x 4 slots of 4 KB per warp: more shared memory than one CTA has
+        with pytest.raises(glm.GLMError) as e:
+            glm.glm_grouped_set_shape(h, 0, 16, 1, 4, 1)
+        assert e.value.status == glm.GLM_ERR_UNSUPPORTED
+        assert glm.glm_grouped_get_shape(h) == before
+    finally:
+        glm.glm_destroy(h)
 
 
 def test_grouped_many_tiny_groups_among_long_ones():
