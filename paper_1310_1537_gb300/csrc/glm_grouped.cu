@@ -166,11 +166,13 @@ __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_ke
         for (int i = 0; i < pre; ++i)
             issue(i);
     }
-    auto load_y = [&](int i) -> float {
+    // a slot's labels are loaded one slot ahead and kept as raw bytes until
+    // their use, so that no conversion waits for the load where it is issued
+    auto load_y = [&](int i) -> unsigned {
         if (i >= nch)
-            return 0.0f;
+            return 0u;
         const int64_t row = wr0 + (int64_t)i * CR + lane;
-        return row < wr1 ? (float)__ldg(p.y + row) : 0.0f;
+        return row < wr1 ? (unsigned)__ldg(p.y + row) : 0u;
     };
 
     // the non-empty group holding row wr0
@@ -295,13 +297,13 @@ __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_ke
 
     if (nch > 0)
         stage_beta(cur);
-    float ycur = load_y(0);
+    unsigned ycur = load_y(0);
     for (int i = 0; i < nch; ++i) {
         const int s = i % stages;
         const unsigned parity = (unsigned)(i / stages) & 1u;
         const int64_t row0 = wr0 + (int64_t)i * CR;
         const int nrows = (int)((wr1 - row0) < CR ? (wr1 - row0) : CR);
-        const float ynext = load_y(i + 1);
+        const unsigned ynext = load_y(i + 1);
         if (!bad) {
             const bool okw = ptx::mbar_wait_bounded(&bars[s], parity, kSpinLimit);
             if (__any_sync(FULL, !okw)) {
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(kGroupedMaxThreads, 1) grouped_logpost_grad_ke
                     eta += pa;
                 }
             }
-            tr_map(eta, ycur, ell, r);
+            tr_map(eta, (float)ycur, ell, r);
         }
 
         // ---- phase 2: per-group segments of this slot ----------------------------
@@ -537,14 +539,15 @@ __global__ void __launch_bounds__(kNarrowMaxThreads, 1)
         for (int i = 0; i < pre; ++i)
             issue(i);
     }
-    // labels of slot i, one register per 32-row unit (at most 4 units)
-    auto load_y = [&](int i, float &a0, float &a1, float &a2, float &a3) {
-        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // labels of slot i, one register per 32-row unit (at most 4 units), kept
+    // as raw bytes until their use one slot later
+    auto load_y = [&](int i, unsigned &a0, unsigned &a1, unsigned &a2, unsigned &a3) {
+        unsigned v[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t row = wr0 + (int64_t)i * SR + u * CR + lane;
             if (i < nch && u < U && row < wr1)
-                v[u] = (float)__ldg(p.y + row);
+                v[u] = (unsigned)__ldg(p.y + row);
         }
         a0 = v[0]; a1 = v[1]; a2 = v[2]; a3 = v[3];
     };
@@ -671,12 +674,12 @@ __global__ void __launch_bounds__(kNarrowMaxThreads, 1)
 
     if (nch > 0)
         load_beta(cur);
-    float yc0, yc1, yc2, yc3;
+    unsigned yc0, yc1, yc2, yc3;
     load_y(0, yc0, yc1, yc2, yc3);
     for (int i = 0; i < nch; ++i) {
         const int s = i % stages;
         const unsigned parity = (unsigned)(i / stages) & 1u;
-        float yn0, yn1, yn2, yn3;
+        unsigned yn0, yn1, yn2, yn3;
         load_y(i + 1, yn0, yn1, yn2, yn3);
         if (!bad) {
             const bool okw = ptx::mbar_wait_bounded(&bars[s], parity, kSpinLimit);
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(kNarrowMaxThreads, 1)
             }
         }
         for (int u = 0; u < U; ++u) {
-            const float ycur = yc0;               // labels shift down one unit per step
+            const float ycur = (float)yc0;        // labels shift down one unit per step
             yc0 = yc1;
             yc1 = yc2;
             yc2 = yc3;
