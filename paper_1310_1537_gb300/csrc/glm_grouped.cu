@@ -10,13 +10,21 @@
 //   phase 1: lane l takes row l of the slot, finds the row's group, computes
 //            eta = x . beta_group and the TR map (ell, r) in FP32;
 //   phase 2: lanes own (row slot, 16-byte column chunk) pairs and accumulate
-//            g += r x for the current group in registers; when the group
-//            ends (or the warp's rows end) the warp adds its f and g sums into
-//            the group's 128-bit fixed-point accumulators.
-// A group's completion counter tells the last contributing warp (the number
-// of warps covering a group follows from the even row split) to add the
-// prior and write f and g. Integer accumulation makes the result independent
-// of arrival order: bitwise reproducible.
+//            g += r x for the current group in registers.
+// When a group ends (or the warp's rows end), a group that lies wholly in
+// the warp's rows is finished from registers (prior added, f and g written);
+// a group shared with neighbouring warps gets the warp's f and g sums in its
+// 128-bit fixed-point accumulators, and its completion counter tells the last
+// contributing warp (the number of warps covering a group follows from the
+// even row split) to add the prior and write f and g. Integer accumulation
+// makes the result independent of arrival order: bitwise reproducible.
+//
+// The kernel has a compile-time instance for rows of eight 16-byte chunks
+// (row stride, chunk rotation and lane mapping constant). A second kernel,
+// for at most 32 used columns, keeps each row, the group's coefficients and
+// the gradient sums in registers. glm_autotune_grouped times both over
+// warps per CTA, rows per slot, ring slots and CTAs per SM;
+// glm_grouped_set_shape sets one of those shapes directly.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
